@@ -1,0 +1,179 @@
+/*
+ * fbpt.h -- C ABI of libfbpt: fused breadth-first probabilistic traversals
+ * (BPTs) on one GB300 GPU, producing reverse-reachable (RR) sets under the
+ * independent-cascade (IC) model and greedy max-coverage seed sets.
+ *
+ * Method: Neff et al., "Fused Breadth-First Probabilistic Traversals on
+ * Distributed GPU Systems" (arXiv 2311.10201).  Section 2 defines the
+ * problem (Definition 1, influence maximization; Definition 2, RR sets) and
+ * the IC model; Section 3 and Listing 1 give the fused traversal, in which the
+ * traversals of many samples share one frontier of per-vertex colour masks;
+ * Section 9 names direction switching, hybrid queue/scan frontiers, dynamic
+ * colour counts and mid-traversal refill as future work, which the scheduler
+ * here implements.
+ *
+ * Conventions shared by every entry point
+ *   - Every function returns FBPT_OK (0) or a negative FBPT_E* status; on
+ *     failure fbpt_last_error() (thread-local) holds a one-line message.
+ *     No C++ exception crosses this boundary.
+ *   - "device" pointers are CUDA global-memory addresses on the current
+ *     device; "host" pointers are ordinary (pageable or pinned) memory.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls enqueue work on it; functions that return host results
+ *     synchronize it before returning.
+ *
+ * Bit-level contract (fixed; every output is a pure function of it):
+ *   Graph: in-edge CSR.  row_ptr[n+1] (uint64, row_ptr[0] = 0, non-decreasing,
+ *     row_ptr[n] = m), col[m] (uint32 < n): row v lists the sources w of the
+ *     edges w -> v.  Edge id e = index into col.  thr[m] (uint32) =
+ *     floor(p(e) * 2^32); 0xFFFFFFFF marks p(e) = 1 (always live).
+ *   Philox4x32-10 (Salmon et al., SC'11), key = (lo32(seed), hi32(seed)).
+ *   Liveness of edge e for sample s (Listing 1's per-colour, per-edge draw
+ *     "random(0,1) > e.prob"): out = Philox(ctr = (lo32(s), hi32(s),
+ *     lo32(e >> 2), hi32(e >> 2))); e is live for s iff thr[e] == 0xFFFFFFFF
+ *     or out[e & 3] < thr[e].  One Philox call serves four consecutive edges
+ *     of one sample.
+ *   Start vertex of sample s (Section 3: starts uniform over V):
+ *     out = Philox(ctr = (lo32(s), hi32(s), 0, 0x80000000)),
+ *     start(s) = floor(((out[1] << 32) | out[0]) * n / 2^64).
+ *   RR set of s (Definition 2): every w with a path w -> ... -> start(s)
+ *     whose edges are all live for s.  Rows are in sample-id order, vertices
+ *     strictly ascending; start(s) is always in its own row.
+ *   Greedy (Section 2, max-k-cover over the RR sets): each pick takes the
+ *     vertex contained in the most not-yet-covered RR sets, the smallest
+ *     vertex id on ties; once every set is covered, the smallest unselected
+ *     id.  Exactly k seeds.
+ */
+#ifndef FBPT_H
+#define FBPT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FBPT_VERSION 1
+
+enum fbpt_status {
+    FBPT_OK = 0,
+    FBPT_EINVAL = -1,       /* bad argument or malformed graph */
+    FBPT_ENOMEM = -2,       /* a device or host allocation failed */
+    FBPT_ECUDA = -3,        /* a CUDA runtime call failed */
+    FBPT_ETIMEOUT = -4,     /* a bounded device wait gave up */
+    FBPT_EUNSUPPORTED = -5, /* option combination not available */
+    FBPT_EDEVICE = -6       /* a kernel's own bounds check tripped */
+};
+
+enum fbpt_mem_kind { FBPT_MEM_HOST = 0, FBPT_MEM_DEVICE = 1 };
+
+/* Level schedule: how each level's frontier is expanded. */
+enum fbpt_schedule {
+    FBPT_SCHED_PUSH = 0,      /* always push over in-edges of frontier vertices */
+    FBPT_SCHED_PULL = 1,      /* always pull over out-edges of unvisited vertices */
+    FBPT_SCHED_HEURISTIC = 2, /* degree-ratio rule picks push or pull per level */
+    FBPT_SCHED_LEARNED = 3    /* policy network picks, heuristic as fallback */
+};
+
+/* How the level loop is driven. */
+enum fbpt_launch {
+    FBPT_LAUNCH_HOST = 0,  /* host launches each level and reads the frontier size back */
+    FBPT_LAUNCH_GRAPH = 1  /* whole sampling run in one CUDA graph (device-side while loop) */
+};
+
+typedef struct fbpt_graph fbpt_graph;
+typedef struct fbpt_policy fbpt_policy;
+
+typedef struct fbpt_opts {
+    uint32_t words;      /* W: 64-colour mask words per batch (1, 2, 4 or 8); 0 = autotune */
+    uint32_t slots;      /* batches traversed concurrently, sharing one frontier; 0 = auto;
+                            words * slots <= 64 */
+    uint32_t schedule;   /* enum fbpt_schedule */
+    uint32_t launch;     /* enum fbpt_launch */
+    uint32_t unfused;    /* 1 = each colour expands its own copy of every edge (no fusing);
+                            output is identical, only the work differs */
+    uint32_t record_trace; /* 1 = keep per-level features/timings (fbpt_trace_*) */
+    const fbpt_policy* policy; /* used by FBPT_SCHED_LEARNED; NULL = built-in heuristic */
+    void* stream;        /* cudaStream_t */
+} fbpt_opts;
+
+/* RR sets as CSR in library-owned device memory (free with fbpt_rrsets_free). */
+typedef struct fbpt_rrsets {
+    uint64_t S;          /* rows */
+    uint64_t total;      /* offsets[S] = sum of row sizes */
+    uint32_t n;          /* vertices of the graph sampled */
+    uint64_t* offsets;   /* device, S+1 */
+    uint32_t* verts;     /* device, total; row j = verts[offsets[j] .. offsets[j+1]) ascending */
+    uint32_t* starts;    /* device, S: start(first_id + j) */
+    uint32_t* vcount;    /* device, n: number of rows containing v (mask popcounts) */
+    void* stream;        /* stream the buffers belong to */
+    void* internal;      /* library bookkeeping */
+} fbpt_rrsets;
+
+typedef struct fbpt_stats {
+    uint64_t levels;              /* expand launches (ticks) */
+    uint64_t batches;             /* 64*W-colour batches traversed */
+    uint64_t push_levels, pull_levels;
+    uint64_t units_expanded;      /* frontier vertices expanded, summed over levels */
+    uint64_t edge_accesses;       /* (frontier vertex, in-edge) pairs read, summed over levels */
+    uint64_t philox_calls;        /* Philox4x32-10 evaluations in expand */
+    uint64_t colour_edge_visits;  /* sum over samples s and v in RR(s) of indeg(v) */
+    uint64_t rr_total;            /* sum of RR set sizes */
+    uint64_t overflow_reruns;     /* batches re-run after the output pool grew */
+    double ms_total;              /* wall time of the call on its stream (CUDA events) */
+    double ms_expand;             /* device time of the expand kernels (CUDA events, HOST launch only) */
+} fbpt_stats;
+
+/* ---- Graphs ---------------------------------------------------------------
+ * Copies the in-edge CSR and thresholds (mem_kind says where the inputs live)
+ * into library-owned device memory; the caller may free its arrays on return.
+ * Validates row_ptr[0] = 0, monotone rows, row_ptr[n] = m, col[e] < n
+ * (FBPT_EINVAL otherwise).  n >= 1, m < 2^40.  thr is kept exactly as given. */
+int fbpt_graph_create(uint32_t n, uint64_t m, const uint64_t* row_ptr, const uint32_t* col,
+                      const uint32_t* thr, int mem_kind, void* stream, fbpt_graph** out);
+int fbpt_graph_destroy(fbpt_graph* g);
+/* n, m and device addresses of the stored arrays (any pointer may be NULL). */
+int fbpt_graph_info(const fbpt_graph* g, uint32_t* n, uint64_t* m, const uint64_t** row_ptr,
+                    const uint32_t** col, const uint32_t** thr);
+
+/* ---- Sampling ----------------------------------------------------------------
+ * RR sets of samples first_id .. first_id + S - 1 (Definition 2, computed by
+ * the fused traversal of Listing 1).  Rows are in sample-id order; results
+ * do not depend on opts (W, slots, schedule, launch, unfused).  out is filled
+ * with library-owned device buffers.  stats may be NULL. */
+int fbpt_sample(fbpt_graph* g, uint64_t seed, uint64_t first_id, uint64_t S, const fbpt_opts* opts,
+                fbpt_rrsets* out, fbpt_stats* stats);
+
+/* Many graphs in one run: graph i gets samples first_ids[i] .. + Ss[i] - 1
+ * under seeds[i]; outs[i] receives its RR sets.  One CUDA graph drives all of
+ * them (opts->launch is ignored); W per graph comes from the autotuner when
+ * opts->words == 0. */
+int fbpt_sample_batched(uint32_t G, fbpt_graph* const* gs, const uint64_t* seeds, const uint64_t* first_ids,
+                        const uint64_t* Ss, const fbpt_opts* opts, fbpt_rrsets* outs, fbpt_stats* stats);
+
+int fbpt_rrsets_free(fbpt_rrsets* rr);
+/* Host copies (any pointer may be NULL): offsets[S+1], verts[total], starts[S], vcount[n]. */
+int fbpt_rrsets_copy_to_host(const fbpt_rrsets* rr, uint64_t* offsets, uint32_t* verts, uint32_t* starts,
+                             uint32_t* vcount);
+
+/* ---- Seed selection -------------------------------------------------------------
+ * Greedy max-k-cover over rr (contract above).  seeds_host[k] receives the
+ * picks in order; gains_host[k] (may be NULL) the number of RR sets each pick
+ * newly covered.  k > rr->n gives FBPT_EINVAL. */
+int fbpt_select_seeds(const fbpt_rrsets* rr, uint32_t k, uint32_t* seeds_host, uint64_t* gains_host);
+
+/* ---- Building blocks exposed for verification ------------------------------------
+ * Device results of the bit-level contract for given inputs (host arrays in
+ * and out, count entries each): edge draws out[e & 3] for pairs (s[i], e[i]),
+ * and start vertices for sample ids. */
+int fbpt_edge_draws(uint64_t seed, const uint64_t* s, const uint64_t* e, uint64_t count, uint32_t* out);
+int fbpt_start_vertices(uint64_t seed, const uint64_t* s, uint64_t count, uint32_t n, uint32_t* out);
+
+const char* fbpt_last_error(void);
+int fbpt_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FBPT_H */
