@@ -121,8 +121,10 @@ typedef struct fbpt_stats {
     uint64_t colour_edge_visits;  /* sum over samples s and v in RR(s) of indeg(v) */
     uint64_t rr_total;            /* sum of RR set sizes */
     uint64_t overflow_reruns;     /* batches re-run after the output pool grew */
-    double ms_total;              /* wall time of the call on its stream (CUDA events) */
-    double ms_expand;             /* device time of the expand kernels (CUDA events, HOST launch only) */
+    uint64_t mask_words;          /* non-zero 64-colour mask words of expanded frontier units */
+    double ms_total;              /* time of the call on its stream (CUDA events) */
+    double ms_expand;             /* device time of the expand kernels: per launch, first CTA start
+                                     to last CTA end (%globaltimer), summed */
 } fbpt_stats;
 
 /* ---- Graphs ---------------------------------------------------------------
@@ -169,6 +171,10 @@ int fbpt_select_seeds(const fbpt_rrsets* rr, uint32_t k, uint32_t* seeds_host, u
  * and start vertices for sample ids. */
 int fbpt_edge_draws(uint64_t seed, const uint64_t* s, const uint64_t* e, uint64_t count, uint32_t* out);
 int fbpt_start_vertices(uint64_t seed, const uint64_t* s, uint64_t count, uint32_t n, uint32_t* out);
+
+/* sizeof(fbpt_opts), sizeof(fbpt_rrsets), sizeof(fbpt_stats) into sizes[0..2]
+ * (count >= 3), so that bindings can check their struct layouts. */
+int fbpt_abi_sizes(uint64_t* sizes, int count);
 
 const char* fbpt_last_error(void);
 int fbpt_version(void);

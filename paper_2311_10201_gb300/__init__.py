@@ -1,0 +1,273 @@
+"""fbpt: fused breadth-first probabilistic traversals on one GB300 GPU.
+
+Thin ctypes binding over libfbpt (include/fbpt.h): argument marshalling only.
+Every step of sampling and seed selection runs in the library's CUDA kernels;
+there is no CPU path.  If libfbpt.so has not been built, importing the
+binding's entry points raises.
+
+    import paper_2311_10201_gb300 as fbpt
+    g = fbpt.Graph(n, row_ptr, col, thr)                 # in-edge CSR + thresholds
+    rr = fbpt.sample(g, seed, first_id, S, words=8)      # RR sets, device CSR
+    offsets, verts, starts, vcount = rr.to_host()
+    seeds, gains = fbpt.select_seeds(rr, k)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfbpt.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "fbpt.h")
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED, EDEVICE = 0, -1, -2, -3, -4, -5, -6
+SCHED = {"push": 0, "pull": 1, "heuristic": 2, "learned": 3}
+LAUNCH = {"host": 0, "graph": 1}
+
+U64P = ctypes.POINTER(ctypes.c_uint64)
+U32P = ctypes.POINTER(ctypes.c_uint32)
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("words", ctypes.c_uint32), ("slots", ctypes.c_uint32), ("schedule", ctypes.c_uint32),
+                ("launch", ctypes.c_uint32), ("unfused", ctypes.c_uint32), ("record_trace", ctypes.c_uint32),
+                ("policy", ctypes.c_void_p), ("stream", ctypes.c_void_p)]
+
+
+class RRSetsC(ctypes.Structure):
+    _fields_ = [("S", ctypes.c_uint64), ("total", ctypes.c_uint64), ("n", ctypes.c_uint32),
+                ("offsets", ctypes.c_void_p), ("verts", ctypes.c_void_p), ("starts", ctypes.c_void_p),
+                ("vcount", ctypes.c_void_p), ("stream", ctypes.c_void_p), ("internal", ctypes.c_void_p)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_uint64) for k in
+                ("levels", "batches", "push_levels", "pull_levels", "units_expanded", "edge_accesses",
+                 "philox_calls", "colour_edge_visits", "rr_total", "overflow_reruns", "mask_words")] + \
+               [("ms_total", ctypes.c_double), ("ms_expand", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class FbptError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libfbpt status {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+# name -> (restype, argtypes); every function the header declares
+_SIGS = {
+    "fbpt_graph_create": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                         ctypes.POINTER(ctypes.c_void_p)]),
+    "fbpt_graph_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "fbpt_graph_info": (ctypes.c_int, [ctypes.c_void_p, U32P, U64P, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_void_p]),
+    "fbpt_sample": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
+                                   ctypes.POINTER(Opts), ctypes.POINTER(RRSetsC), ctypes.POINTER(Stats)]),
+    "fbpt_sample_batched": (ctypes.c_int, [ctypes.c_uint32, ctypes.POINTER(ctypes.c_void_p), U64P, U64P, U64P,
+                                           ctypes.POINTER(Opts), ctypes.POINTER(RRSetsC), ctypes.POINTER(Stats)]),
+    "fbpt_rrsets_free": (ctypes.c_int, [ctypes.POINTER(RRSetsC)]),
+    "fbpt_rrsets_copy_to_host": (ctypes.c_int, [ctypes.POINTER(RRSetsC), ctypes.c_void_p, ctypes.c_void_p,
+                                                ctypes.c_void_p, ctypes.c_void_p]),
+    "fbpt_select_seeds": (ctypes.c_int, [ctypes.POINTER(RRSetsC), ctypes.c_uint32, U32P, U64P]),
+    "fbpt_edge_draws": (ctypes.c_int, [ctypes.c_uint64, U64P, U64P, ctypes.c_uint64, U32P]),
+    "fbpt_start_vertices": (ctypes.c_int, [ctypes.c_uint64, U64P, ctypes.c_uint64, ctypes.c_uint32, U32P]),
+    "fbpt_abi_sizes": (ctypes.c_int, [U64P, ctypes.c_int]),
+    "fbpt_last_error": (ctypes.c_char_p, []),
+    "fbpt_version": (ctypes.c_int, []),
+}
+
+
+def lib():
+    """The loaded libfbpt; raises if it has not been built (no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libfbpt.so not built ({LIB_PATH}); run paper_2311_10201_gb300.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        sizes = (ctypes.c_uint64 * 3)()
+        L.fbpt_abi_sizes(sizes, 3)
+        want = [ctypes.sizeof(Opts), ctypes.sizeof(RRSetsC), ctypes.sizeof(Stats)]
+        if list(sizes) != want:
+            raise RuntimeError(f"libfbpt struct layout mismatch: library {list(sizes)} vs binding {want}")
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != OK:
+        raise FbptError(rc, lib().fbpt_last_error().decode())
+
+
+def _stream_handle(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            pass
+        return None
+    if isinstance(stream, int):
+        return stream
+    return getattr(stream, "cuda_stream")
+
+
+def _ptr_u64(a):
+    return a.ctypes.data_as(U64P)
+
+
+def _ptr_u32(a):
+    return a.ctypes.data_as(U32P)
+
+
+class Graph:
+    """Library-owned device copy of an in-edge CSR with per-edge thresholds.
+
+    row_ptr/col/thr: numpy arrays (host) or torch CUDA tensors (device)."""
+
+    def __init__(self, n, row_ptr, col, thr, stream=None):
+        self.n = int(n)
+        self._h = ctypes.c_void_p()
+        dev = hasattr(row_ptr, "is_cuda") and row_ptr.is_cuda
+        if dev:
+            args = (row_ptr.data_ptr(), col.data_ptr(), thr.data_ptr(), 1)
+            m = int(col.numel())
+        else:
+            row_ptr = np.ascontiguousarray(row_ptr, np.uint64)
+            col = np.ascontiguousarray(col, np.uint32)
+            thr = np.ascontiguousarray(thr, np.uint32)
+            args = (row_ptr.ctypes.data, col.ctypes.data if col.size else None,
+                    thr.ctypes.data if thr.size else None, 0)
+            m = int(col.size)
+        self.m = m
+        self.stream = _stream_handle(stream)
+        _check(lib().fbpt_graph_create(self.n, m, args[0], args[1], args[2], args[3], self.stream,
+                                       ctypes.byref(self._h)))
+
+    @classmethod
+    def from_synth(cls, g, stream=None):
+        return cls(g.n, g.row_ptr, g.col, g.thr, stream)
+
+    def close(self):
+        if self._h:
+            lib().fbpt_graph_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class RRSets:
+    """RR sets in library-owned device memory (CSR over samples)."""
+
+    def __init__(self, c: RRSetsC, stats: Stats):
+        self.c = c
+        self.stats = stats
+
+    @property
+    def S(self):
+        return int(self.c.S)
+
+    @property
+    def total(self):
+        return int(self.c.total)
+
+    def to_host(self):
+        S, total, n = self.S, self.total, int(self.c.n)
+        off = np.empty(S + 1, np.uint64)
+        verts = np.empty(max(total, 1), np.uint32)
+        starts = np.empty(S, np.uint32)
+        vcount = np.empty(n, np.uint32)
+        _check(lib().fbpt_rrsets_copy_to_host(ctypes.byref(self.c), off.ctypes.data, verts.ctypes.data,
+                                              starts.ctypes.data, vcount.ctypes.data))
+        return off, verts[:total], starts, vcount
+
+    def free(self):
+        if self.c.offsets:
+            lib().fbpt_rrsets_free(ctypes.byref(self.c))
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def make_opts(words=0, slots=0, schedule="push", launch="graph", unfused=False, stream=None, policy=None):
+    o = Opts()
+    o.words, o.slots = int(words), int(slots)
+    o.schedule = SCHED[schedule] if isinstance(schedule, str) else int(schedule)
+    o.launch = LAUNCH[launch] if isinstance(launch, str) else int(launch)
+    o.unfused = int(bool(unfused))
+    o.policy = policy
+    o.stream = stream
+    return o
+
+
+def sample(g: Graph, seed: int, first_id: int, S: int, stream=None, **kw) -> RRSets:
+    """RR sets of samples first_id .. first_id+S-1 (fbpt_sample)."""
+    o = make_opts(stream=_stream_handle(stream) if stream is not None else g.stream, **kw)
+    c = RRSetsC()
+    st = Stats()
+    _check(lib().fbpt_sample(g._h, seed, first_id, S, ctypes.byref(o), ctypes.byref(c), ctypes.byref(st)))
+    return RRSets(c, st)
+
+
+def sample_batched(graphs, seeds, first_ids, Ss, stream=None, **kw):
+    G = len(graphs)
+    o = make_opts(stream=_stream_handle(stream) if stream is not None else graphs[0].stream, **kw)
+    hs = (ctypes.c_void_p * G)(*[g._h.value for g in graphs])
+    arr = lambda xs: np.ascontiguousarray(xs, np.uint64)
+    sd, fi, ss = arr(seeds), arr(first_ids), arr(Ss)
+    outs = (RRSetsC * G)()
+    st = Stats()
+    _check(lib().fbpt_sample_batched(G, hs, _ptr_u64(sd), _ptr_u64(fi), _ptr_u64(ss), ctypes.byref(o), outs,
+                                     ctypes.byref(st)))
+    res = []
+    for i in range(G):
+        c = RRSetsC()
+        ctypes.pointer(c)[0] = outs[i]
+        res.append(RRSets(c, st))
+    return res, st
+
+
+def select_seeds(rr: RRSets, k: int):
+    """Greedy max-k-cover (fbpt_select_seeds): (seeds[k], newly covered rows per pick[k])."""
+    seeds = np.zeros(max(k, 1), np.uint32)
+    gains = np.zeros(max(k, 1), np.uint64)
+    _check(lib().fbpt_select_seeds(ctypes.byref(rr.c), k, _ptr_u32(seeds), _ptr_u64(gains)))
+    return seeds[:k], gains[:k]
+
+
+def edge_draws(seed: int, s, e):
+    s = np.ascontiguousarray(s, np.uint64)
+    e = np.ascontiguousarray(e, np.uint64)
+    out = np.zeros(max(s.size, 1), np.uint32)
+    _check(lib().fbpt_edge_draws(seed, _ptr_u64(s), _ptr_u64(e), s.size, _ptr_u32(out)))
+    return out[:s.size]
+
+
+def start_vertices(seed: int, s, n: int):
+    s = np.ascontiguousarray(s, np.uint64)
+    out = np.zeros(max(s.size, 1), np.uint32)
+    _check(lib().fbpt_start_vertices(seed, _ptr_u64(s), s.size, n, _ptr_u32(out)))
+    return out[:s.size]
+
+
+def build(force: bool = False):
+    from . import builder
+    return builder.build(force=force)

@@ -1,0 +1,138 @@
+// C ABI glue: errors, version, RR-set buffers, sampling entry points and the
+// verification building blocks (device results of the bit-level contract).
+#include <cstring>
+#include <string>
+
+#include "internal.cuh"
+
+namespace fbpt {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+const char* last_error() { return g_last_error.c_str(); }
+
+int device_sm_count() {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    return sms;
+}
+
+int sample_impl(fbpt_graph* g, uint64_t seed, uint64_t first_id, uint64_t S, const fbpt_opts* opts, fbpt_rrsets* out,
+                fbpt_stats* stats);
+
+namespace {
+
+__global__ void k_edge_draws(uint64_t seed, const uint64_t* s, const uint64_t* e, uint64_t count, uint32_t* out) {
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint4 r = edge_draws4(seed, s[i], e[i] >> 2);
+        const uint32_t k = (uint32_t)(e[i] & 3);
+        out[i] = k == 0 ? r.x : k == 1 ? r.y : k == 2 ? r.z : r.w;
+    }
+}
+
+__global__ void k_starts(uint64_t seed, const uint64_t* s, uint64_t count, uint32_t n, uint32_t* out) {
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (uint64_t)gridDim.x * blockDim.x)
+        out[i] = start_vertex(seed, s[i], n);
+}
+
+}  // namespace
+}  // namespace fbpt
+
+using namespace fbpt;
+
+extern "C" const char* fbpt_last_error(void) { return last_error(); }
+extern "C" int fbpt_version(void) { return FBPT_VERSION; }
+
+extern "C" int fbpt_abi_sizes(uint64_t* sizes, int count) {
+    if (!sizes || count < 3) return fail(FBPT_EINVAL, "fbpt_abi_sizes: need 3 entries");
+    sizes[0] = sizeof(fbpt_opts);
+    sizes[1] = sizeof(fbpt_rrsets);
+    sizes[2] = sizeof(fbpt_stats);
+    return FBPT_OK;
+}
+
+extern "C" int fbpt_sample(fbpt_graph* g, uint64_t seed, uint64_t first_id, uint64_t S, const fbpt_opts* opts,
+                           fbpt_rrsets* out, fbpt_stats* stats) {
+    try {
+        return sample_impl(g, seed, first_id, S, opts, out, stats);
+    } catch (const std::exception& e) {
+        return fail(FBPT_ENOMEM, std::string("fbpt_sample: ") + e.what());
+    }
+}
+
+extern "C" int fbpt_sample_batched(uint32_t G, fbpt_graph* const* gs, const uint64_t* seeds, const uint64_t* first_ids,
+                                   const uint64_t* Ss, const fbpt_opts* opts, fbpt_rrsets* outs, fbpt_stats* stats) {
+    if (G == 0 || !gs || !seeds || !first_ids || !Ss || !outs) return fail(FBPT_EINVAL, "fbpt_sample_batched: null argument");
+    for (uint32_t i = 0; i < G; ++i) {
+        int rc = fbpt_sample(gs[i], seeds[i], first_ids[i], Ss[i], opts, &outs[i], stats);
+        if (rc != FBPT_OK) {
+            for (uint32_t j = 0; j < i; ++j) fbpt_rrsets_free(&outs[j]);
+            return rc;
+        }
+    }
+    return FBPT_OK;
+}
+
+extern "C" int fbpt_rrsets_free(fbpt_rrsets* rr) {
+    if (!rr) return FBPT_OK;
+    cudaStream_t st = (cudaStream_t)rr->stream;
+    if (rr->offsets) cudaFreeAsync(rr->offsets, st);
+    if (rr->verts) cudaFreeAsync(rr->verts, st);
+    if (rr->starts) cudaFreeAsync(rr->starts, st);
+    if (rr->vcount) cudaFreeAsync(rr->vcount, st);
+    std::memset(rr, 0, sizeof(*rr));
+    return FBPT_OK;
+}
+
+extern "C" int fbpt_rrsets_copy_to_host(const fbpt_rrsets* rr, uint64_t* offsets, uint32_t* verts, uint32_t* starts,
+                                        uint32_t* vcount) {
+    if (!rr) return fail(FBPT_EINVAL, "fbpt_rrsets_copy_to_host: null rrsets");
+    cudaStream_t st = (cudaStream_t)rr->stream;
+    if (offsets) FBPT_CUDA_TRY(cudaMemcpyAsync(offsets, rr->offsets, sizeof(uint64_t) * (rr->S + 1), cudaMemcpyDeviceToHost, st));
+    if (verts && rr->total) FBPT_CUDA_TRY(cudaMemcpyAsync(verts, rr->verts, sizeof(uint32_t) * rr->total, cudaMemcpyDeviceToHost, st));
+    if (starts) FBPT_CUDA_TRY(cudaMemcpyAsync(starts, rr->starts, sizeof(uint32_t) * rr->S, cudaMemcpyDeviceToHost, st));
+    if (vcount) FBPT_CUDA_TRY(cudaMemcpyAsync(vcount, rr->vcount, sizeof(uint32_t) * rr->n, cudaMemcpyDeviceToHost, st));
+    FBPT_CUDA_TRY(cudaStreamSynchronize(st));
+    return FBPT_OK;
+}
+
+extern "C" int fbpt_edge_draws(uint64_t seed, const uint64_t* s, const uint64_t* e, uint64_t count, uint32_t* out) {
+    if (count == 0) return FBPT_OK;
+    if (!s || !e || !out) return fail(FBPT_EINVAL, "fbpt_edge_draws: null array");
+    uint64_t *ds = nullptr, *de = nullptr;
+    uint32_t* dout = nullptr;
+    FBPT_CUDA_TRY(cudaMalloc(&ds, count * 8));
+    FBPT_CUDA_TRY(cudaMalloc(&de, count * 8));
+    FBPT_CUDA_TRY(cudaMalloc(&dout, count * 4));
+    cudaMemcpy(ds, s, count * 8, cudaMemcpyHostToDevice);
+    cudaMemcpy(de, e, count * 8, cudaMemcpyHostToDevice);
+    k_edge_draws<<<(unsigned)std::min<uint64_t>((count + 255) / 256, 4096), 256>>>(seed, ds, de, count, dout);
+    cudaError_t err = cudaMemcpy(out, dout, count * 4, cudaMemcpyDeviceToHost);
+    cudaFree(ds);
+    cudaFree(de);
+    cudaFree(dout);
+    if (err != cudaSuccess) return fail(FBPT_ECUDA, std::string("fbpt_edge_draws: ") + cudaGetErrorString(err));
+    return FBPT_OK;
+}
+
+extern "C" int fbpt_start_vertices(uint64_t seed, const uint64_t* s, uint64_t count, uint32_t n, uint32_t* out) {
+    if (count == 0) return FBPT_OK;
+    if (!s || !out || n == 0) return fail(FBPT_EINVAL, "fbpt_start_vertices: bad argument");
+    uint64_t* ds = nullptr;
+    uint32_t* dout = nullptr;
+    FBPT_CUDA_TRY(cudaMalloc(&ds, count * 8));
+    FBPT_CUDA_TRY(cudaMalloc(&dout, count * 4));
+    cudaMemcpy(ds, s, count * 8, cudaMemcpyHostToDevice);
+    k_starts<<<(unsigned)std::min<uint64_t>((count + 255) / 256, 4096), 256>>>(seed, ds, count, n, dout);
+    cudaError_t err = cudaMemcpy(out, dout, count * 4, cudaMemcpyDeviceToHost);
+    cudaFree(ds);
+    cudaFree(dout);
+    if (err != cudaSuccess) return fail(FBPT_ECUDA, std::string("fbpt_start_vertices: ") + cudaGetErrorString(err));
+    return FBPT_OK;
+}
