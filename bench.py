@@ -126,7 +126,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--words", type=int, default=8)
     ap.add_argument("--slots", type=int, default=0)
-    ap.add_argument("--launch", default="graph")
+    ap.add_argument("--launch", default="persistent")
     ap.add_argument("--samples", type=int, default=1 << 20)
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()

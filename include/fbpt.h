@@ -79,23 +79,36 @@ enum fbpt_schedule {
 /* How the level loop is driven. */
 enum fbpt_launch {
     FBPT_LAUNCH_HOST = 0,  /* host launches each level and reads the frontier size back */
-    FBPT_LAUNCH_GRAPH = 1  /* whole sampling run in one CUDA graph (device-side while loop) */
+    FBPT_LAUNCH_GRAPH = 1, /* per-level kernels looped inside one CUDA graph (WHILE conditional node) */
+    FBPT_LAUNCH_PERSISTENT = 2 /* one cooperative persistent kernel; levels separated by bounded
+                                  grid barriers (FBPT_ETIMEOUT if a wait gives up) */
+};
+
+/* When a colour lane takes its next sample. */
+enum fbpt_refill {
+    FBPT_REFILL_LANE = 0,  /* as soon as the lane's traversal ends (mid-traversal injection) */
+    FBPT_REFILL_BATCH = 1  /* only when every lane of the row has finished: the plain fused
+                              algorithm with 64 * words * slots colours per group */
 };
 
 typedef struct fbpt_graph fbpt_graph;
 typedef struct fbpt_policy fbpt_policy;
 
 typedef struct fbpt_opts {
-    uint32_t words;      /* W: 64-colour mask words per batch (1, 2, 4 or 8); 0 = autotune */
-    uint32_t slots;      /* batches traversed concurrently, sharing one frontier; 0 = auto;
-                            words * slots <= 64 */
+    uint32_t words;      /* W: 64-colour mask words per batch (1, 2, 4 or 8); 0 = 8 */
+    uint32_t slots;      /* batches traversed concurrently, sharing one frontier; 0 = 64 / words.
+                            A vertex row holds words * slots <= 64 words, i.e. that many
+                            64-colour lanes groups; each colour lane carries one sample */
     uint32_t schedule;   /* enum fbpt_schedule */
     uint32_t launch;     /* enum fbpt_launch */
     uint32_t unfused;    /* 1 = each colour expands its own copy of every edge (no fusing);
                             output is identical, only the work differs */
+    uint32_t refill;     /* enum fbpt_refill */
     uint32_t record_trace; /* 1 = keep per-level features/timings (fbpt_trace_*) */
     const fbpt_policy* policy; /* used by FBPT_SCHED_LEARNED; NULL = built-in heuristic */
     void* stream;        /* cudaStream_t */
+    uint64_t spin_limit; /* FBPT_LAUNCH_PERSISTENT: polls before a grid-barrier wait gives up
+                            (0 = default, about a few seconds) */
 } fbpt_opts;
 
 /* RR sets as CSR in library-owned device memory (free with fbpt_rrsets_free). */
@@ -123,8 +136,10 @@ typedef struct fbpt_stats {
     uint64_t overflow_reruns;     /* batches re-run after the output pool grew */
     uint64_t mask_words;          /* non-zero 64-colour mask words of expanded frontier units */
     double ms_total;              /* time of the call on its stream (CUDA events) */
-    double ms_expand;             /* device time of the expand kernels: per launch, first CTA start
+    double ms_expand;             /* device time of the expand phase: per level, first CTA start
                                      to last CTA end (%globaltimer), summed */
+    double ms_commit;             /* same for the commit phase */
+    double ms_sweep;              /* same for the sweep phase (RR pairs of finished lanes) */
 } fbpt_stats;
 
 /* ---- Graphs ---------------------------------------------------------------

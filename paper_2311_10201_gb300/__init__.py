@@ -24,7 +24,7 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "fbpt.h")
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED, EDEVICE = 0, -1, -2, -3, -4, -5, -6
 SCHED = {"push": 0, "pull": 1, "heuristic": 2, "learned": 3}
-LAUNCH = {"host": 0, "graph": 1}
+LAUNCH = {"host": 0, "graph": 1, "persistent": 2}
 
 U64P = ctypes.POINTER(ctypes.c_uint64)
 U32P = ctypes.POINTER(ctypes.c_uint32)
@@ -32,8 +32,9 @@ U32P = ctypes.POINTER(ctypes.c_uint32)
 
 class Opts(ctypes.Structure):
     _fields_ = [("words", ctypes.c_uint32), ("slots", ctypes.c_uint32), ("schedule", ctypes.c_uint32),
-                ("launch", ctypes.c_uint32), ("unfused", ctypes.c_uint32), ("record_trace", ctypes.c_uint32),
-                ("policy", ctypes.c_void_p), ("stream", ctypes.c_void_p)]
+                ("launch", ctypes.c_uint32), ("unfused", ctypes.c_uint32), ("refill", ctypes.c_uint32),
+                ("record_trace", ctypes.c_uint32),
+                ("policy", ctypes.c_void_p), ("stream", ctypes.c_void_p), ("spin_limit", ctypes.c_uint64)]
 
 
 class RRSetsC(ctypes.Structure):
@@ -46,7 +47,8 @@ class Stats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_uint64) for k in
                 ("levels", "batches", "push_levels", "pull_levels", "units_expanded", "edge_accesses",
                  "philox_calls", "colour_edge_visits", "rr_total", "overflow_reruns", "mask_words")] + \
-               [("ms_total", ctypes.c_double), ("ms_expand", ctypes.c_double)]
+               [("ms_total", ctypes.c_double), ("ms_expand", ctypes.c_double), ("ms_commit", ctypes.c_double),
+                ("ms_sweep", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -207,8 +209,14 @@ class RRSets:
             pass
 
 
-def make_opts(words=0, slots=0, schedule="push", launch="graph", unfused=False, stream=None, policy=None):
+REFILL = {"lane": 0, "batch": 1}
+
+
+def make_opts(words=0, slots=0, schedule="push", launch="persistent", unfused=False, stream=None, policy=None,
+              spin_limit=0, refill="lane"):
     o = Opts()
+    o.refill = REFILL[refill] if isinstance(refill, str) else int(refill)
+    o.spin_limit = int(spin_limit)
     o.words, o.slots = int(words), int(slots)
     o.schedule = SCHED[schedule] if isinstance(schedule, str) else int(schedule)
     o.launch = LAUNCH[launch] if isinstance(launch, str) else int(launch)

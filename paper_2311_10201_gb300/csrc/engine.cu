@@ -1,23 +1,29 @@
-// The fused-BPT sampling engine (Section 3, Listing 1; Section 9 future-work
-// items (a) and (b)).
+// The fused-BPT sampling engine (Section 3, Listing 1), with the adaptive
+// future-work items of Section 9: (b) finished traversals hand their RR sets
+// over early and new starts are injected mid-traversal.
 //
-// Colours.  A vertex row holds WB = B * W 64-bit words.  Word i belongs to
-// slot k = i / W; a slot traverses one batch of 64*W consecutive samples, and
-// colour c of the slot is sample slot_base[k] + c.  All slots share one
+// Colour lanes.  A vertex row holds WB 64-bit words, i.e. 64*WB colour lanes.
+// Each lane carries one sample at a time: bit c of word i of visited[v] means
+// "the sample held by lane 64i+c has reached v".  All lanes share one
 // frontier: a frontier unit is a vertex with the non-zero words of its new
-// colour mask, so the in-edges of a vertex are read once per level for every
-// colour of every slot that reached it (Listing 1's "fusing" line, widened
-// across batches).  When a slot's colours are all finished, its RR sets are
-// dumped and the slot takes the next batch without stopping the others
-// (mid-traversal refill).
+// mask, and the in-edges of a unit are read once per level for all of its
+// colours (Listing 1's fusing update, over every sample in flight).  When a
+// lane's sample stops (no unit carries its bit), the next level sweeps the
+// lane's own list of reached vertices (a segment of kSegCap entries, then a
+// shared spill log) into (sample, vertex) pairs, clears the lane's bit from
+// visited[], and the lane takes the next sample id (lane refill); or, in
+// batch mode, lanes wait until the whole row has finished, which is the plain
+// fused algorithm of Listing 1 with 64*WB colours per group.
 //
-// One level ("tick") is five kernels, all launched with fixed grids so that a
-// CUDA graph can loop them on the device:
-//   expand   frontier units x 4-edge groups -> next masks, pending vertices
-//   commit   pending vertices -> visited, new frontier list, touched lists
-//   schedule (1 CTA) finished slots, refills, loop condition
-//   dump     RR pairs (sample, vertex) of finished slots; clears their state
-//   init     start vertices of newly assigned batches
+// One level ("tick") has five phases:
+//   sweep    finished lanes: RR pairs out, bits cleared, spill log compacted
+//   init     start vertices of lanes assigned a new sample
+//   expand   frontier units x 4-edge groups -> next rows, pending vertices
+//   commit   pending vertices -> visited, new frontier list, lane entry lists
+//   schedule (one CTA) finished lanes, refills, loop condition
+// They run as five kernels per level (host loop or CUDA-graph WHILE loop) or
+// inside one persistent cooperative kernel, where sweep, init and expand of
+// a level share a phase and bounded grid barriers separate the phases.
 //
 // Liveness never reads visited[]: the expand draws for every colour of the
 // frontier mask and the commit removes colours a vertex has already seen.
@@ -25,56 +31,160 @@
 // the hot loop streams col/thr with 128-bit loads instead of gathering masks.
 #include <algorithm>
 #include <cstring>
-#include <vector>
+#include <string>
 
 #include "internal.cuh"
 
 namespace fbpt {
 namespace {
 
-constexpr int kExpThreads = 256;
-constexpr int kComThreads = 256;
-constexpr int kAuxThreads = 256;
+constexpr int kThreads = 256;
 
 __device__ __forceinline__ uint64_t row_groups(uint64_t rs, uint64_t re) {
     return re > rs ? ((re - 1) >> 2) - (rs >> 2) + 1 : 0;
 }
 
-// Bit k set iff slot k has a non-zero word in occ (words k*W .. k*W+W-1).
-__device__ __forceinline__ uint64_t slots_of(uint64_t occ, uint32_t W) {
-    if (W == 1) return occ;
-    const uint64_t wm = (1ull << W) - 1;
-    uint64_t s = 0;
-    for (uint32_t k = 0; occ; ++k, occ >>= W)
-        if (occ & wm) s |= 1ull << k;
-    return s;
+// Data written by other CTAs in an earlier phase of the persistent kernel is
+// read through L2 (ld.global.cg), never from a possibly stale L1 line.
+template <typename T>
+__device__ __forceinline__ T L2(const T* p) { return __ldcg(p); }
+
+struct Smem {
+    uint32_t lane[kMaxLanes + 1];   // expand: sample index per lane; sweep, schedule: entry prefixes
+    uint64_t act[kMaxWords];        // commit: lanes seen in this CTA's new units
+    uint64_t fin[kMaxWords];        // sweep: finished lanes (spill-log sweep)
+    uint32_t cnt[kMaxWords + 1];    // schedule: per-word counts, then their prefix
+    uint32_t tsum[kThreads + 1];    // schedule: per-thread sums of the block scan
+    uint32_t last, abort;
+};
+
+__device__ __forceinline__ void phase_begin(Ctl* ctl, int p) {
+    if (threadIdx.x == 0) atomicMin(&ctl->ph_t0[p], globaltimer_ns());
+}
+__device__ __forceinline__ void phase_end(Ctl* ctl, int p) {
+    __syncthreads();
+    if (threadIdx.x == 0) atomicMax(&ctl->ph_t1[p], globaltimer_ns());
 }
 
-__device__ __forceinline__ void mark_dirty(const Eng& E, uint32_t w) {
-    const unsigned long long bit = 1ull << (w & 63);
-    const unsigned long long old = atomicOr((unsigned long long*)&E.dirty[w >> 6], bit);
-    if (!(old & bit)) {
-        const uint32_t p = atomicAdd(&E.ctl->pend_count, 1u);
-        if (p < E.pend_cap)
-            E.pend_v[p] = w;
-        else
-            atomicOr(&E.ctl->error, (unsigned)kErrPendOverflow);
+// w becomes pending (once per level) when the first word of next[w] turns non-zero.
+__device__ __forceinline__ void or_next(const Eng& E, uint32_t w, uint32_t i, uint64_t y) {
+    const unsigned long long old =
+        atomicOr((unsigned long long*)&E.next[(uint64_t)w * E.WB + i], (unsigned long long)y);
+    if (old != 0) return;
+    const unsigned long long o2 = atomicOr((unsigned long long*)&E.nocc[w], 1ull << i);
+    if (o2 != 0) return;
+    const uint32_t p = atomicAdd(&E.ctl->pend_count, 1u);
+    if (p < E.pend_cap)
+        E.pend_v[p] = w;
+    else
+        atomicOr(&E.ctl->error, (unsigned)kErrPendOverflow);
+}
+
+// ---- sweep: RR pairs of finished lanes (Listing 1's RRR-set construction) ------------------
+
+// Every entry of a finished lane (its segment, plus the spill log when the
+// segment overflowed) is one (sample, vertex) pair of its RR set; the lane's
+// bit is cleared from visited[] so that the lane can carry its next sample.
+__device__ __forceinline__ void sweep_entry(const Eng& E, uint32_t l, uint32_t v, uint64_t& cev) {
+    atomicAnd((unsigned long long*)&E.visited[(uint64_t)v * E.WB + (l >> 6)], ~(1ull << (l & 63)));
+    atomicAdd(&E.vcount[v], 1u);
+    cev += __ldg(&E.row_ptr[v + 1]) - __ldg(&E.row_ptr[v]);
+}
+
+__device__ void dev_sweep(const Eng& E, Smem& sm) {
+    Ctl* ctl = E.ctl;
+    const uint32_t F = L2(&ctl->fin_count);
+    const uint32_t spill = L2(&ctl->spill_sweep);
+    if (F == 0 && !spill) return;
+    phase_begin(ctl, 2);
+    __syncthreads();
+    for (uint32_t k = threadIdx.x; k <= F; k += blockDim.x) sm.lane[k] = L2(&ctl->fin_pre[k]);
+    for (uint32_t i = threadIdx.x; i < E.WB; i += blockDim.x) sm.fin[i] = L2(&ctl->fin_mask[i]);
+    __syncthreads();
+    const uint32_t total = sm.lane[F];
+    const uint32_t lane = lane_id();
+    const uint64_t wid = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarp = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const uint64_t cap = L2(&ctl->pair_cap);
+    uint64_t cev = 0;
+    for (uint64_t base = wid * 32; base < total; base += nwarp * 32) {
+        const uint32_t idx = (uint32_t)(base + lane);
+        const bool ok = idx < total;
+        uint32_t l = 0, v = 0;
+        if (ok) {
+            uint32_t lo = 0, hi = F;  // largest k < F with prefix[k] <= idx
+            while (hi - lo > 1) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (sm.lane[mid] <= idx) lo = mid; else hi = mid;
+            }
+            l = L2(&ctl->fin_lane[lo]);
+            v = L2(&E.seg[(uint64_t)l * kSegCap + (idx - sm.lane[lo])]);
+        }
+        const uint64_t pos = warp_alloc<unsigned long long>(&ctl->pair_cursor, ok ? 1ull : 0ull);
+        if (ok) {
+            if (pos < cap) E.pairs[pos] = ((uint64_t)L2(&ctl->retired_j[l]) << E.vbits) | v;
+            sweep_entry(E, l, v, cev);
+        }
+    }
+    if (spill) {
+        const uint32_t dst = L2(&ctl->spill_cur), src = dst ^ 1u;
+        const uint64_t len = min((uint64_t)L2(&ctl->spill_len[src]), E.spill_cap);
+        for (uint64_t base = wid * 32; base < len; base += nwarp * 32) {
+            const uint64_t idx = base + lane;
+            const bool ok = idx < len;
+            uint32_t l = 0, v = 0;
+            bool done = false;
+            uint64_t ent = 0;
+            if (ok) {
+                ent = L2(&E.spill[(uint64_t)src * E.spill_cap + idx]);
+                l = (uint32_t)(ent >> 32);
+                v = (uint32_t)ent;
+                done = (sm.fin[l >> 6] >> (l & 63)) & 1ull;
+            }
+            const uint64_t pos = warp_alloc<unsigned long long>(&ctl->pair_cursor, (ok && done) ? 1ull : 0ull);
+            const uint64_t kp = warp_alloc<unsigned long long>(&ctl->spill_len[dst], (ok && !done) ? 1ull : 0ull);
+            if (ok && done) {
+                if (pos < cap) E.pairs[pos] = ((uint64_t)L2(&ctl->retired_j[l]) << E.vbits) | v;
+                sweep_entry(E, l, v, cev);
+            } else if (ok) {
+                if (kp < E.spill_cap) E.spill[(uint64_t)dst * E.spill_cap + kp] = ent;
+                else atomicOr(&ctl->error, (unsigned)kErrSpillOverflow);
+            }
+        }
+    }
+    cev = warp_sum(cev);
+    if (lane == 0 && cev) atomicAdd(&ctl->st_cev, (unsigned long long)cev);
+    phase_end(ctl, 2);
+}
+
+// ---- init: start vertices of lanes given a new sample (Listing 1's frontier initialization) ------
+
+__device__ void dev_init(const Eng& E) {
+    Ctl* ctl = E.ctl;
+    const uint64_t lanes = 64ull * E.WB;
+    for (uint64_t l = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; l < lanes;
+         l += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t i = (uint32_t)(l >> 6), c = (uint32_t)(l & 63);
+        if (!((L2(&ctl->init_w[i]) >> c) & 1ull)) continue;
+        const uint32_t j = L2(&ctl->lane_j[l]);
+        const uint32_t v = start_vertex(E.seed, E.first_id + j, E.n);
+        E.starts[j] = v;
+        or_next(E, v, i, 1ull << c);
     }
 }
 
 // ---- expand (push over in-edges) -----------------------------------------------------
 
-// One 4-edge group of frontier unit u: edges 4q .. 4q+3 of the in-row of v,
-// with q = rs/4 + j.  For each colour of the unit one Philox call decides all
-// four edges (Listing 1's per-colour liveness draw); live colours are ORed
-// into next[w] (Listing 1's fusing update).
-__device__ __forceinline__ void expand_group(const Eng& E, uint32_t u, uint64_t j, const uint64_t* s_wbase,
+// One 4-edge group of frontier unit u: edges 4q .. 4q+3 of the in-row [rs, re)
+// of its vertex, q = rs/4 + j.  For each colour of the unit one Philox call
+// decides all four edges (Listing 1's per-colour liveness draw); live colours
+// are ORed into next[w] (Listing 1's fusing update).
+__device__ __forceinline__ void expand_group(const Eng& E, const Smem& sm, uint32_t u, uint64_t j,
                                              uint64_t& n_edges, uint64_t& n_calls) {
-    const uint32_t v = E.list_v[u];
-    const uint64_t occ = E.list_occ[u];
-    const uint32_t mrow = E.list_mrow[u];
-    const uint32_t only = E.unfused ? E.list_only[u] : 0u;
-    const uint64_t rs = E.row_ptr[v], re = E.row_ptr[v + 1];
+    const uint64_t occ = L2(&E.list_occ[u]);
+    const uint32_t mrow = L2(&E.list_mrow[u]);
+    const uint64_t rs = L2(&E.list_rs[u]), re = L2(&E.list_re[u]);
+    const uint32_t only = E.unfused ? L2(&E.list_only[u]) : 0u;
     const uint64_t q = (rs >> 2) + j;
     const uint64_t e0 = q << 2;
     const uint4 c4 = __ldg(reinterpret_cast<const uint4*>(E.col) + q);
@@ -88,21 +198,19 @@ __device__ __forceinline__ void expand_group(const Eng& E, uint32_t u, uint64_t 
     // A draw is needed only for edges with 0 < thr < 0xFFFFFFFF.
     const bool need = (t4.x - 1u < 0xFFFFFFFEu) || (t4.y - 1u < 0xFFFFFFFEu) || (t4.z - 1u < 0xFFFFFFFEu) ||
                       (t4.w - 1u < 0xFFFFFFFEu);
-    bool a0 = false, a1 = false, a2 = false, a3 = false;
     uint64_t words = occ;
     while (words) {
         const uint32_t i = __ffsll((long long)words) - 1;
         words &= words - 1;
-        const uint64_t x = only ? (1ull << ((only - 1u) & 63u)) : E.stage[(uint64_t)mrow * E.WB + i];
+        const uint64_t x = only ? (1ull << ((only - 1u) & 63u)) : L2(&E.stage[(uint64_t)mrow * E.WB + i]);
         uint64_t y0, y1, y2, y3;
         if (need) {
             y0 = y1 = y2 = y3 = 0;
-            const uint64_t sb = s_wbase[i];
             uint64_t xx = x;
             while (xx) {
                 const uint32_t c = __ffsll((long long)xx) - 1;
                 xx &= xx - 1;
-                const uint4 r = edge_draws4(E.seed, sb + c, q);
+                const uint4 r = edge_draws4(E.seed, E.first_id + sm.lane[(i << 6) + c], q);
                 ++n_calls;
                 const uint64_t bit = 1ull << c;
                 if (live(r.x, t4.x)) y0 |= bit;
@@ -116,135 +224,142 @@ __device__ __forceinline__ void expand_group(const Eng& E, uint32_t u, uint64_t 
             y2 = t4.z ? x : 0;
             y3 = t4.w ? x : 0;
         }
-        if (y0) { atomicOr((unsigned long long*)&E.next[(uint64_t)c4.x * E.WB + i], y0); a0 = true; }
-        if (y1) { atomicOr((unsigned long long*)&E.next[(uint64_t)c4.y * E.WB + i], y1); a1 = true; }
-        if (y2) { atomicOr((unsigned long long*)&E.next[(uint64_t)c4.z * E.WB + i], y2); a2 = true; }
-        if (y3) { atomicOr((unsigned long long*)&E.next[(uint64_t)c4.w * E.WB + i], y3); a3 = true; }
+        if (y0) or_next(E, c4.x, i, y0);
+        if (y1) or_next(E, c4.y, i, y1);
+        if (y2) or_next(E, c4.z, i, y2);
+        if (y3) or_next(E, c4.w, i, y3);
     }
-    if (a0) mark_dirty(E, c4.x);
-    if (a1) mark_dirty(E, c4.y);
-    if (a2) mark_dirty(E, c4.z);
-    if (a3) mark_dirty(E, c4.w);
 }
 
-// Persistent, edge-balanced: CTAs take tiles of kTileGroups consecutive groups
-// of the frontier's group space from an atomic counter; the unit of each group
-// is found by binary search over the units' group offsets staged in shared
-// memory.
-__global__ void __launch_bounds__(kExpThreads) k_expand(const Eng E) {
-    __shared__ uint64_t s_gb[kTileGroups + 1];
-    __shared__ uint64_t s_wbase[kMaxWords];
-    __shared__ uint32_t s_tile;
+// Edge-balanced: the frontier's 4-edge groups form one index space; a warp
+// takes kChunksPerGrab chunks of 32 consecutive groups per atomic, one group
+// per lane.  chunk_u0[c] names the unit holding group 32c; the lanes find
+// their own unit among the (at most 32) units of the chunk by binary lifting
+// over shuffled group offsets.
+__device__ void dev_expand(const Eng& E, Smem& sm) {
     Ctl* ctl = E.ctl;
-    const uint64_t G = ctl->list_groups;
+    const uint64_t G = L2(&ctl->list_groups);
     if (G == 0) return;
-    if (threadIdx.x == 0) atomicMin(&ctl->exp_t0, globaltimer_ns());
-    const uint64_t U = ctl->list_count;
-    for (uint32_t i = threadIdx.x; i < E.WB; i += blockDim.x)
-        s_wbase[i] = ctl->slot_base[i / E.W] + 64ull * (i % E.W);
-    const uint64_t ntiles = (G + kTileGroups - 1) / kTileGroups;
-    if (ntiles > E.tile_cap || U > E.list_cap) return;  // overflow already flagged by commit
+    const uint64_t U = L2(&ctl->list_count);
+    const uint64_t nchunks = (G + kChunk - 1) / kChunk;
+    if (nchunks > E.chunk_cap || U > E.list_cap) return;  // overflow already flagged by commit
+    phase_begin(ctl, 0);
+    __syncthreads();
+    for (uint32_t l = threadIdx.x; l < 64u * E.WB; l += blockDim.x) sm.lane[l] = L2(&ctl->lane_j[l]);
+    __syncthreads();
+    const uint32_t lane = lane_id();
     uint64_t n_edges = 0, n_calls = 0;
     for (;;) {
-        __syncthreads();
-        if (threadIdx.x == 0) s_tile = atomicAdd(&ctl->tile_next, 1u);
-        __syncthreads();
-        const uint64_t t = s_tile;
-        if (t >= ntiles) break;
-        const uint64_t g0 = t * kTileGroups;
-        const uint64_t g1 = min(g0 + kTileGroups, G);
-        const uint32_t u0 = E.tile_u0[t];
-        const uint32_t u1 = (t + 1 < ntiles) ? E.tile_u0[t + 1] : (uint32_t)(U - 1);
-        const uint32_t nu = u1 - u0 + 1;
-        for (uint32_t i = threadIdx.x; i < nu; i += blockDim.x) s_gb[i] = E.list_g[u0 + i];
-        __syncthreads();
-        for (uint64_t g = g0 + threadIdx.x; g < g1; g += blockDim.x) {
-            uint32_t lo = 0, hi = nu;
-            while (hi - lo > 1) {
-                const uint32_t mid = (lo + hi) >> 1;
-                if (s_gb[mid] <= g) lo = mid; else hi = mid;
+        uint32_t c0 = 0;
+        if (lane == 0) c0 = atomicAdd(&ctl->chunk_next, kChunksPerGrab);
+        c0 = __shfl_sync(0xffffffffu, c0, 0);
+        if (c0 >= nchunks) break;
+        const uint32_t c1 = (uint32_t)min((uint64_t)c0 + kChunksPerGrab, nchunks);
+        for (uint32_t c = c0; c < c1; ++c) {
+            const uint64_t g = (uint64_t)c * kChunk + lane;
+            const uint32_t u0 = L2(&E.chunk_u0[c]);
+            const uint32_t ul = (c + 1 < nchunks) ? L2(&E.chunk_u0[c + 1]) : (uint32_t)(U - 1);
+            const uint32_t nu = min(ul - u0 + 1u, 32u);
+            const uint64_t gb = lane < nu ? L2(&E.list_g[u0 + lane]) : ~0ull;
+            uint32_t k = 0;
+#pragma unroll
+            for (uint32_t step = 16; step > 0; step >>= 1) {
+                const uint64_t gs = __shfl_sync(0xffffffffu, gb, (k + step) & 31u);
+                if (k + step < nu && gs <= g) k += step;
             }
-            expand_group(E, u0 + lo, g - s_gb[lo], s_wbase, n_edges, n_calls);
+            const uint64_t gk = __shfl_sync(0xffffffffu, gb, k);
+            if (g < G) expand_group(E, sm, u0 + k, g - gk, n_edges, n_calls);
         }
     }
     n_edges = warp_sum(n_edges);
     n_calls = warp_sum(n_calls);
-    if (lane_id() == 0) {
+    if (lane == 0) {
         if (n_edges) atomicAdd(&ctl->st_edges, (unsigned long long)n_edges);
         if (n_calls) atomicAdd(&ctl->st_calls, (unsigned long long)n_calls);
     }
-    __syncthreads();
-    if (threadIdx.x == 0) atomicMax(&ctl->exp_t1, globaltimer_ns());
+    phase_end(ctl, 0);
 }
 
 // ---- commit -------------------------------------------------------------------------
 
 __device__ __forceinline__ void write_unit(const Eng& E, uint64_t pos, uint32_t w, uint32_t mrow, uint64_t occ,
-                                           uint32_t only, uint64_t gbeg, uint64_t ng) {
+                                           uint32_t only, uint64_t rs, uint64_t re, uint64_t gbeg, uint64_t ng) {
     E.list_v[pos] = w;
     E.list_mrow[pos] = mrow;
     E.list_occ[pos] = occ;
+    E.list_rs[pos] = rs;
+    E.list_re[pos] = re;
     E.list_g[pos] = gbeg;
     if (E.unfused) E.list_only[pos] = only;
-    // tiles whose first group falls inside this unit start their search here
+    // chunks whose first group falls inside this unit start their search here
     const uint64_t end = gbeg + ng;
-    for (uint64_t t = (gbeg + kTileGroups - 1) / kTileGroups; t * kTileGroups < end; ++t) {
-        if (t < E.tile_cap) E.tile_u0[t] = (uint32_t)pos;
-        else atomicOr(&E.ctl->error, (unsigned)kErrTileOverflow);
+    for (uint64_t c = (gbeg + kChunk - 1) / kChunk; c * kChunk < end; ++c) {
+        if (c < E.chunk_cap) E.chunk_u0[c] = (uint32_t)pos;
+        else atomicOr(&E.ctl->error, (unsigned)kErrChunkOverflow);
     }
 }
 
-// For every pending vertex w: nx = next[w] & ~visited[w]; next[w] = 0;
-// visited[w] |= nx.  Non-empty nx becomes a frontier unit (if w has in-edges);
-// the first colour of a slot to reach w appends w to that slot's touched list.
-__global__ void __launch_bounds__(kComThreads) k_commit(const Eng E) {
+// For every pending vertex w and every word i with next[w][i] != 0:
+// nx = next[w][i] & ~visited[w][i]; next[w][i] = 0; visited[w][i] |= nx.
+// Non-empty rows become frontier units (if w has in-edges); w joins word i's
+// touched list when it is the first colour of that word to reach w.
+__device__ void dev_commit(const Eng& E, Smem& sm) {
     Ctl* ctl = E.ctl;
-    const uint32_t P = (uint32_t)min((uint64_t)ctl->pend_count, E.pend_cap);
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < E.WB; i += blockDim.x) sm.act[i] = 0;
+    __syncthreads();
+    const uint32_t P = (uint32_t)min((uint64_t)L2(&ctl->pend_count), E.pend_cap);
+    if (P) phase_begin(ctl, 1);
+    const uint32_t spill_cur = L2(&ctl->spill_cur);
     const uint32_t lane = lane_id();
-    uint64_t mwords = 0;
     const uint64_t wid = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarp = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    uint64_t active = 0;
+    uint64_t mwords = 0;
     for (uint64_t base = wid * 32; base < P; base += nwarp * 32) {
         const uint64_t idx = base + lane;
         const bool ok = idx < P;
         uint32_t w = 0, bits = 0;
         uint64_t occ = 0, rs = 0, re = 0;
         if (ok) {
-            w = E.pend_v[idx];
-            E.dirty[w >> 6] = 0ull;  // every dirty bit of this word belongs to a pending vertex
-            const uint64_t rowb = (uint64_t)w * E.WB;
-            for (uint32_t i = 0; i < E.WB; ++i) {
-                uint64_t nx = E.next[rowb + i];
-                if (!nx) continue;
-                E.next[rowb + i] = 0;
-                const uint64_t vis = E.visited[rowb + i];
+            w = L2(&E.pend_v[idx]);
+            uint64_t m = L2(&E.nocc[w]);
+            E.nocc[w] = 0;
+            rs = __ldg(&E.row_ptr[w]);
+            re = __ldg(&E.row_ptr[w + 1]);
+            const bool has_edges = re > rs;
+            while (m) {
+                const uint32_t i = __ffsll((long long)m) - 1;
+                m &= m - 1;
+                const uint64_t rowi = (uint64_t)w * E.WB + i;
+                uint64_t nx = L2(&E.next[rowi]);
+                E.next[rowi] = 0;
+                const uint64_t vis = L2(&E.visited[rowi]);
                 nx &= ~vis;
                 if (!nx) continue;
-                E.visited[rowb + i] = vis | nx;
+                E.visited[rowi] = vis | nx;
                 E.stage[idx * E.WB + i] = nx;
                 occ |= 1ull << i;
                 bits += __popcll(nx);
-            }
-            uint64_t so = slots_of(occ, E.W);
-            const uint64_t bit = 1ull << (w & 63);
-            while (so) {
-                const uint32_t k = __ffsll((long long)so) - 1;
-                so &= so - 1;
-                const unsigned long long old = atomicOr((unsigned long long*)&E.touched[k * E.nw + (w >> 6)], bit);
-                if (!(old & bit)) {
-                    const uint32_t t = atomicAdd(&ctl->tcount[k], 1u);
-                    E.tlist[(uint64_t)k * E.n + t] = w;
+                // each new colour adds w to its lane's RR entries
+                uint64_t nb = nx;
+                while (nb) {
+                    const uint32_t c = __ffsll((long long)nb) - 1;
+                    nb &= nb - 1;
+                    const uint32_t l = (i << 6) + c;
+                    const uint32_t pos = atomicAdd(&ctl->lane_cnt[l], 1u);
+                    if (pos < kSegCap) {
+                        E.seg[(uint64_t)l * kSegCap + pos] = w;
+                    } else {
+                        const uint64_t sp = atomicAdd(&ctl->spill_len[spill_cur], 1ull);
+                        if (sp < E.spill_cap) E.spill[(uint64_t)spill_cur * E.spill_cap + sp] = ((uint64_t)l << 32) | w;
+                        else atomicOr(&ctl->error, (unsigned)kErrSpillOverflow);
+                    }
                 }
-            }
-            if (occ) {
-                rs = E.row_ptr[w];
-                re = E.row_ptr[w + 1];
+                if (has_edges) atomicOr((unsigned long long*)&sm.act[i], (unsigned long long)nx);
             }
         }
-        const uint64_t ng = row_groups(rs, re);
+        const uint64_t ng = occ ? row_groups(rs, re) : 0;
         const uint64_t units = ng ? (E.unfused ? bits : 1u) : 0u;
-        if (units) active |= slots_of(occ, E.W);
         mwords += units ? (E.unfused ? units : (uint64_t)__popcll(occ)) : 0;
         const unsigned long long req = (unsigned long long)((units * ng) << kUnitBits) | units;
         const unsigned long long got = warp_alloc<unsigned long long>(&ctl->new_packed, req);
@@ -254,7 +369,7 @@ __global__ void __launch_bounds__(kComThreads) k_commit(const Eng E) {
             if (pos + units > E.list_cap) {
                 atomicOr(&ctl->error, (unsigned)kErrListOverflow);
             } else if (!E.unfused) {
-                write_unit(E, pos, w, (uint32_t)idx, occ, 0u, gbeg, ng);
+                write_unit(E, pos, w, (uint32_t)idx, occ, 0u, rs, re, gbeg, ng);
             } else {
                 uint64_t ws = occ;
                 while (ws) {
@@ -264,169 +379,259 @@ __global__ void __launch_bounds__(kComThreads) k_commit(const Eng E) {
                     while (x) {
                         const uint32_t c = __ffsll((long long)x) - 1;
                         x &= x - 1;
-                        write_unit(E, pos++, w, (uint32_t)idx, 1ull << i, i * 64u + c + 1u, gbeg, ng);
+                        write_unit(E, pos++, w, (uint32_t)idx, 1ull << i, i * 64u + c + 1u, rs, re, gbeg, ng);
                         gbeg += ng;
                     }
                 }
             }
         }
     }
-    active = warp_or64(active);
     mwords = warp_sum(mwords);
-    if (lane == 0 && active) atomicOr(&ctl->active_mask, (unsigned long long)active);
     if (lane == 0 && mwords) atomicAdd(&ctl->st_mask_words, (unsigned long long)mwords);
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < E.WB; i += blockDim.x)
+        if (sm.act[i]) atomicOr(&ctl->act_w[i], (unsigned long long)sm.act[i]);
+    if (P) phase_end(ctl, 1);
 }
 
-// ---- schedule (one CTA of kMaxSlots threads) ---------------------------------------------
+// ---- schedule (one CTA, at least kMaxWords threads) ------------------------------------
 
-__global__ void k_schedule(const Eng E) {
+// Lanes that held a sample but are absent from the new frontier have finished
+// (the next sweep emits them).  Free lanes take the next sample ids, right away
+// (lane refill) or once no lane is still traversing (batch mode).  The new
+// frontier list becomes the expand's input; the loop continues while any
+// lane holds a sample.
+__device__ void dev_schedule(const Eng& E, Smem& sm) {
     Ctl* ctl = E.ctl;
-    __shared__ uint32_t s_fin, s_init, s_run;
-    if (threadIdx.x == 0) { s_fin = 0; s_init = 0; s_run = 0; }
+    const uint32_t i = threadIdx.x;
+    const bool mine = i < E.WB;
+    const uint32_t err = L2(&ctl->error);
+    uint64_t still = 0, fin = 0;
+    if (mine) {
+        const uint64_t run = L2(&ctl->run_w[i]);
+        const uint64_t act = L2(&ctl->act_w[i]);
+        still = run & act;
+        fin = run & ~act;
+        sm.cnt[i] = __popcll(fin);
+    }
+    const bool any_still = __syncthreads_or(still != 0);
+    // finished lanes, word by word: base index of each word's finished lanes
+    if (threadIdx.x == 0) {
+        uint32_t acc = 0;
+        for (uint32_t w = 0; w < E.WB; ++w) {
+            const uint32_t c = sm.cnt[w];
+            sm.cnt[w] = acc;
+            acc += c;
+        }
+        sm.cnt[E.WB] = acc;
+    }
     __syncthreads();
-    const uint64_t act = ctl->active_mask;
-    const uint32_t k = threadIdx.x;
-    if (k < E.B) {
-        uint32_t st = ctl->slot_state[k];
-        if (st == kSlotRunning && !((act >> k) & 1ull)) {
-            const uint32_t f = atomicAdd(&s_fin, 1u);
-            ctl->fin_slot[f] = k;
-            ctl->fin_base[f] = ctl->slot_base[k];
-            ctl->fin_ncol[f] = ctl->slot_ncol[k];
-            st = kSlotIdle;
+    const uint32_t F = sm.cnt[E.WB];
+    bool spilled = false;
+    if (mine) {
+        uint32_t k = sm.cnt[i];
+        uint64_t f = fin;
+        while (f) {
+            const uint32_t c = __ffsll((long long)f) - 1;
+            f &= f - 1;
+            const uint32_t l = (i << 6) + c;
+            const uint32_t rc = L2(&ctl->lane_cnt[l]);
+            ctl->retired_j[l] = L2(&ctl->lane_j[l]);
+            ctl->lane_cnt[l] = 0;
+            ctl->fin_lane[k] = l;
+            sm.lane[k] = min(rc, kSegCap);
+            spilled |= rc > kSegCap;
+            ++k;
         }
-        if (st == kSlotIdle && ctl->error == 0) {
-            const unsigned long long b = atomicAdd(&ctl->next_batch, 1ull);
-            if (b < ctl->nbatches) {
-                const uint64_t colours = 64ull * E.W;
-                const uint64_t s0 = b * colours;
-                ctl->slot_base[k] = E.first_id + s0;
-                ctl->slot_ncol[k] = (uint32_t)min(colours, E.S - s0);
-                ctl->init_slot[atomicAdd(&s_init, 1u)] = k;
-                st = kSlotRunning;
+        ctl->fin_mask[i] = fin;
+    }
+    const bool any_spill = __syncthreads_or(spilled);
+    // exclusive prefix of the finished lanes' segment entry counts
+    {
+        const uint32_t per = (F + blockDim.x - 1) / blockDim.x;
+        const uint32_t a0 = min(threadIdx.x * per, F), a1 = min(a0 + per, F);
+        uint32_t t = 0;
+        for (uint32_t k = a0; k < a1; ++k) t += sm.lane[k];
+        sm.tsum[threadIdx.x] = t;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t acc = 0;
+            for (uint32_t q = 0; q < blockDim.x; ++q) {
+                const uint32_t x = sm.tsum[q];
+                sm.tsum[q] = acc;
+                acc += x;
             }
+            sm.tsum[blockDim.x] = acc;
         }
-        ctl->slot_state[k] = st;
-        if (st == kSlotRunning) atomicOr(&s_run, 1u);
+        __syncthreads();
+        uint32_t run = sm.tsum[threadIdx.x];
+        for (uint32_t k = a0; k < a1; ++k) {
+            const uint32_t x = sm.lane[k];
+            ctl->fin_pre[k] = run;
+            run += x;
+        }
+        if (threadIdx.x == 0) {
+            ctl->fin_pre[F] = sm.tsum[blockDim.x];
+            ctl->fin_count = F;
+        }
+    }
+    __syncthreads();
+    const bool may_refill = err == 0 && (L2(&ctl->refill) == kRefillLane || !any_still);
+    uint64_t need = 0;
+    if (mine) {
+        need = may_refill ? ~still : 0ull;
+        sm.cnt[i] = __popcll(need);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        ctl->fin_count = s_fin;
-        ctl->init_count = s_init;
-        ctl->st_batches += s_init;
-        const unsigned long long np = ctl->new_packed;
-        ctl->list_count = np & kUnitMask;
-        ctl->list_groups = np >> kUnitBits;
-        if (ctl->error) {  // a capacity check tripped: expand nothing more
-            ctl->list_count = 0;
-            ctl->list_groups = 0;
+        uint32_t acc = 0;
+        for (uint32_t w = 0; w < E.WB; ++w) {
+            const uint32_t c = sm.cnt[w];
+            sm.cnt[w] = acc;
+            acc += c;
         }
+        sm.cnt[E.WB] = acc;
+    }
+    __syncthreads();
+    const uint64_t base_j = L2(&ctl->next_j);
+    const uint64_t avail = E.S > base_j ? E.S - base_j : 0;
+    uint64_t init = 0;
+    if (mine) {
+        uint64_t r = sm.cnt[i];
+        uint64_t nd = need;
+        while (nd && r < avail) {
+            const uint32_t c = __ffsll((long long)nd) - 1;
+            nd &= nd - 1;
+            ctl->lane_j[(i << 6) + c] = (uint32_t)(base_j + r);
+            init |= 1ull << c;
+            ++r;
+        }
+        ctl->init_w[i] = init;
+        ctl->run_w[i] = still | init;
+        ctl->act_w[i] = 0;
+    }
+    const bool any_run = __syncthreads_or((still | init) != 0);
+    if (threadIdx.x == 0) {
+        // a lane whose segment overflowed has entries in the spill log: the next
+        // sweep reads the log and writes the surviving entries to the other buffer
+        if (any_spill) {
+            const uint32_t dst = L2(&ctl->spill_cur) ^ 1u;
+            ctl->spill_cur = dst;
+            ctl->spill_len[dst] = 0;
+        }
+        ctl->spill_sweep = any_spill ? 1u : 0u;
+        const uint64_t assigned = min((uint64_t)sm.cnt[E.WB], avail);
+        ctl->next_j = base_j + assigned;
+        ctl->st_assigned += assigned;
+        const unsigned long long np = L2(&ctl->new_packed);
+        ctl->list_count = err ? 0 : (np & kUnitMask);
+        ctl->list_groups = err ? 0 : (np >> kUnitBits);
         ctl->st_units += np & kUnitMask;
         if ((np >> kUnitBits) != 0) ctl->st_push += 1;
-        if (ctl->exp_t1 > ctl->exp_t0) ctl->st_expand_ns += ctl->exp_t1 - ctl->exp_t0;
-        ctl->exp_t0 = ~0ull;
-        ctl->exp_t1 = 0;
-        ctl->new_packed = 0;
-        ctl->tile_next = 0;
-        ctl->pend_count = 0;
-        ctl->active_mask = 0;
-        ctl->tick += 1;
-        uint32_t run = s_run;
-        if (ctl->tick > ctl->tick_limit) {
-            ctl->error |= kErrTickLimit;
+        for (int p = 0; p < 3; ++p) {
+            const unsigned long long t0 = L2(&ctl->ph_t0[p]), t1 = L2(&ctl->ph_t1[p]);
+            if (t1 > t0) ctl->st_phase_ns[p] += t1 - t0;
+            ctl->ph_t0[p] = ~0ull;
+            ctl->ph_t1[p] = 0;
         }
-        if (ctl->error) run = 0;
+        ctl->new_packed = 0;
+        ctl->chunk_next = 0;
+        ctl->pend_count = 0;
+        const unsigned long long tick = L2(&ctl->tick) + 1;
+        ctl->tick = tick;
+        uint32_t run = any_run ? 1u : 0u;
+        if (tick > L2(&ctl->tick_limit)) {
+            atomicOr(&ctl->error, (unsigned)kErrTickLimit);
+            run = 0;
+        }
+        if (err) run = 0;
         ctl->running = run;
+        __threadfence();
         if (E.cond) cudaGraphSetConditional((cudaGraphConditionalHandle)E.cond, run);
     }
+    __syncthreads();
 }
 
-// ---- dump: RR pairs of finished slots (Listing 1's RRR-set construction) -------------------
+// ---- per-level kernels (host-driven or CUDA-graph loop) ------------------------------------
 
-__global__ void __launch_bounds__(kAuxThreads) k_dump(const Eng E) {
+__global__ void __launch_bounds__(kThreads) k_sweep(const Eng E) {
+    __shared__ Smem sm;
+    dev_sweep(E, sm);
+}
+__global__ void __launch_bounds__(kThreads) k_init(const Eng E) { dev_init(E); }
+__global__ void __launch_bounds__(kThreads) k_expand(const Eng E) {
+    __shared__ Smem sm;
+    dev_expand(E, sm);
+}
+__global__ void __launch_bounds__(kThreads) k_commit(const Eng E) {
+    __shared__ Smem sm;
+    dev_commit(E, sm);
+}
+__global__ void __launch_bounds__(kThreads) k_schedule(const Eng E) {
+    __shared__ Smem sm;
+    dev_schedule(E, sm);
+}
+
+// ---- persistent form: the whole run in one cooperative launch -------------------------------
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid-wide barrier with a bounded wait.  The last CTA to arrive optionally
+// runs the scheduler before releasing the others.  Returns false when a wait
+// gave up (error bit set; the caller returns).
+__device__ bool grid_barrier(const Eng& E, Smem& sm, unsigned& gen, bool schedule) {
     Ctl* ctl = E.ctl;
-    const uint32_t F = ctl->fin_count;
-    if (F == 0) return;
-    __shared__ uint64_t s_pre[kMaxSlots + 1];
-    __shared__ uint32_t s_slot[kMaxSlots];
-    __shared__ uint64_t s_base[kMaxSlots];
+    __syncthreads();
     if (threadIdx.x == 0) {
-        s_pre[0] = 0;
-        for (uint32_t f = 0; f < F; ++f) {
-            s_slot[f] = ctl->fin_slot[f];
-            s_base[f] = ctl->fin_base[f] - E.first_id;
-            s_pre[f + 1] = s_pre[f] + ctl->tcount[s_slot[f]];
-        }
+        sm.abort = 0;
+        __threadfence();
+        const unsigned arrived = atomicAdd(&ctl->bar_count, 1u) + 1u;
+        sm.last = arrived == gridDim.x;
     }
     __syncthreads();
-    const uint64_t total = s_pre[F];
-    const uint32_t lane = lane_id();
-    const uint64_t wid = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint64_t nwarp = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    const uint64_t cap = ctl->pair_cap;
-    uint64_t cev = 0;
-    for (uint64_t base = wid * 32; base < total; base += nwarp * 32) {
-        const uint64_t idx = base + lane;
-        const bool ok = idx < total;
-        uint64_t x[8];
-        uint32_t cnt = 0, v = 0, f = 0;
-        if (ok) {
-            while (s_pre[f + 1] <= idx) ++f;
-            const uint32_t k = s_slot[f];
-            v = E.tlist[(uint64_t)k * E.n + (idx - s_pre[f])];
-            const uint64_t rowb = (uint64_t)v * E.WB + (uint64_t)k * E.W;
-#pragma unroll
-            for (uint32_t w = 0; w < 8; ++w) {
-                x[w] = 0;
-                if (w < E.W) {
-                    x[w] = E.visited[rowb + w];
-                    E.visited[rowb + w] = 0;
-                    cnt += __popcll(x[w]);
-                }
-            }
-            E.touched[(uint64_t)k * E.nw + (v >> 6)] = 0ull;  // all its bits are in this dump
-            atomicAdd(&E.vcount[v], cnt);
-            cev += (uint64_t)cnt * (E.row_ptr[v + 1] - E.row_ptr[v]);
+    if (sm.last) {
+        __threadfence();
+        if (schedule) dev_schedule(E, sm);
+        if (threadIdx.x == 0) {
+            ctl->bar_count = 0;
+            __threadfence();
+            atomicAdd(&ctl->bar_gen, 1u);
         }
-        uint64_t pos = warp_alloc<unsigned long long>(&ctl->pair_cursor, (unsigned long long)cnt);
-        if (ok && pos + cnt <= cap) {
-            const uint64_t jb = s_base[f];
-#pragma unroll
-            for (uint32_t w = 0; w < 8; ++w) {
-                uint64_t xx = x[w];
-                while (xx) {
-                    const uint32_t c = __ffsll((long long)xx) - 1;
-                    xx &= xx - 1;
-                    E.pairs[pos++] = ((jb + 64ull * w + c) << E.vbits) | v;
-                }
+    } else if (threadIdx.x == 0) {
+        unsigned long long spins = 0;
+        while (ld_acquire_u32(&ctl->bar_gen) == gen) {
+            if (++spins > E.spin_limit || (L2(&ctl->error) & kErrBarrierTimeout)) {
+                atomicOr(&ctl->error, (unsigned)kErrBarrierTimeout);
+                sm.abort = 1;
+                break;
             }
+            __nanosleep(32);
         }
+        __threadfence();
     }
-    cev = warp_sum(cev);
-    if (lane == 0 && cev) atomicAdd(&ctl->st_cev, (unsigned long long)cev);
+    ++gen;
+    __syncthreads();
+    return !sm.abort;
 }
 
-// ---- init: start vertices of newly assigned batches (Listing 1's frontier initialization) --------
-
-__global__ void __launch_bounds__(kAuxThreads) k_init(const Eng E) {
+__global__ void __launch_bounds__(kThreads) k_run(const Eng E) {
+    __shared__ Smem sm;
     Ctl* ctl = E.ctl;
-    const uint32_t I = ctl->init_count;
-    const uint32_t F = ctl->fin_count;
-    const uint64_t gt = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    if (gt < F) ctl->tcount[ctl->fin_slot[gt]] = 0;
-    const uint64_t colours = 64ull * E.W;
-    const uint64_t total = (uint64_t)I * colours;
-    for (uint64_t idx = gt; idx < total; idx += stride) {
-        const uint32_t k = ctl->init_slot[idx / colours];
-        const uint32_t c = (uint32_t)(idx % colours);
-        if (c >= ctl->slot_ncol[k]) continue;
-        const uint64_t s = ctl->slot_base[k] + c;
-        const uint32_t v = start_vertex(E.seed, s, E.n);
-        E.starts[s - E.first_id] = v;
-        atomicOr((unsigned long long*)&E.next[(uint64_t)v * E.WB + (uint64_t)k * E.W + (c >> 6)], 1ull << (c & 63));
-        mark_dirty(E, v);
+    unsigned gen = 0;
+    for (;;) {
+        dev_sweep(E, sm);  // lanes finished at the previous level
+        dev_init(E);       // lanes given a sample at the previous level
+        dev_expand(E, sm);
+        if (!grid_barrier(E, sm, gen, false)) return;
+        dev_commit(E, sm);
+        if (!grid_barrier(E, sm, gen, true)) return;
+        if (!L2(&ctl->running)) break;
     }
+    dev_sweep(E, sm);
 }
 
 // ---- finalize: sorted pairs -> CSR --------------------------------------------------------
@@ -445,7 +650,7 @@ __global__ void k_finalize(const uint64_t* keys, uint64_t total, uint32_t vbits,
 }
 
 struct LaunchShape {
-    int expand_blocks = 0, commit_blocks = 0, aux_blocks = 0;
+    int level_blocks = 0, run_blocks = 0;
 };
 
 LaunchShape launch_shape() {
@@ -454,28 +659,47 @@ LaunchShape launch_shape() {
     if (!done) {
         const int sms = device_sm_count();
         int per = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_expand, kExpThreads, 0);
-        ls.expand_blocks = sms * std::max(per, 1);
-        ls.commit_blocks = sms * 4;
-        ls.aux_blocks = sms * 2;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_expand, kThreads, 0);
+        ls.level_blocks = sms * std::max(per, 1);
+        per = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_run, kThreads, 0);
+        ls.run_blocks = sms * std::max(per, 1);
         done = true;
     }
     return ls;
 }
 
-int launch_tick(const Eng& E, cudaStream_t st) {
+int launch_level(const Eng& E, cudaStream_t st) {
     const LaunchShape ls = launch_shape();
-    k_expand<<<ls.expand_blocks, kExpThreads, 0, st>>>(E);
-    k_commit<<<ls.commit_blocks, kComThreads, 0, st>>>(E);
-    k_schedule<<<1, kMaxSlots, 0, st>>>(E);
-    k_dump<<<ls.aux_blocks, kAuxThreads, 0, st>>>(E);
-    k_init<<<ls.aux_blocks, kAuxThreads, 0, st>>>(E);
+    k_sweep<<<ls.level_blocks, kThreads, 0, st>>>(E);
+    k_init<<<std::min(ls.level_blocks, (int)(64 * E.WB + kThreads - 1) / kThreads), kThreads, 0, st>>>(E);
+    k_expand<<<ls.level_blocks, kThreads, 0, st>>>(E);
+    k_commit<<<ls.level_blocks, kThreads, 0, st>>>(E);
+    k_schedule<<<1, kThreads, 0, st>>>(E);
     FBPT_CUDA_TRY(cudaGetLastError());
     return FBPT_OK;
 }
 
-// The whole run as one CUDA graph: a WHILE conditional node whose body is one
-// tick; k_schedule sets the condition.
+int launch_final_sweep(const Eng& E, cudaStream_t st) {
+    k_sweep<<<launch_shape().level_blocks, kThreads, 0, st>>>(E);
+    FBPT_CUDA_TRY(cudaGetLastError());
+    return FBPT_OK;
+}
+
+int run_persistent(const Eng& E, cudaStream_t st) {
+    const LaunchShape ls = launch_shape();
+    Eng e = E;
+    void* args[] = {(void*)&e};
+    cudaError_t err = cudaLaunchCooperativeKernel((const void*)k_run, dim3(ls.run_blocks), dim3(kThreads), args, 0, st);
+    if (err != cudaSuccess) {
+        cudaGetLastError();
+        return fail(FBPT_ECUDA, std::string("cooperative launch: ") + cudaGetErrorString(err));
+    }
+    return FBPT_OK;
+}
+
+// The level loop as one CUDA graph: a WHILE conditional node whose body is
+// one level; the scheduler sets the condition.
 int run_graph(Eng E, cudaStream_t st) {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -510,7 +734,7 @@ int run_graph(Eng E, cudaStream_t st) {
             rc = fail(FBPT_ECUDA, "cudaStreamBeginCaptureToGraph failed");
             break;
         }
-        int lrc = launch_tick(E, cs);
+        int lrc = launch_level(E, cs);
         cudaGraph_t captured = nullptr;
         cudaError_t ce = cudaStreamEndCapture(cs, &captured);
         cudaStreamDestroy(cs);
@@ -524,6 +748,8 @@ int run_graph(Eng E, cudaStream_t st) {
             rc = fail(FBPT_ECUDA, "cudaGraphLaunch failed");
             break;
         }
+        E.cond = 0;
+        rc = launch_final_sweep(E, st);
     } while (0);
     if (exec) {
         cudaStreamSynchronize(st);
@@ -549,24 +775,26 @@ int dalloc(T** p, uint64_t count, size_t& bytes) {
 
 void ws_free(Workspace* w) {
     if (!w) return;
-    cudaFree(w->visited); cudaFree(w->next); cudaFree(w->stage); cudaFree(w->dirty); cudaFree(w->touched);
-    cudaFree(w->tlist); cudaFree(w->pend_v); cudaFree(w->list_v); cudaFree(w->list_mrow); cudaFree(w->list_only);
-    cudaFree(w->list_g); cudaFree(w->list_occ); cudaFree(w->tile_u0); cudaFree(w->ctl);
+    cudaFree(w->visited); cudaFree(w->next); cudaFree(w->nocc); cudaFree(w->stage); cudaFree(w->pend_v);
+    cudaFree(w->seg); cudaFree(w->spill); cudaFree(w->list_v); cudaFree(w->list_mrow); cudaFree(w->list_only); cudaFree(w->list_rs);
+    cudaFree(w->list_re); cudaFree(w->list_g); cudaFree(w->list_occ); cudaFree(w->chunk_u0); cudaFree(w->ctl);
     if (w->ctl_host) cudaFreeHost(w->ctl_host);
     delete w;
 }
 
-int ws_get(fbpt_graph* g, uint32_t W, uint32_t B, bool unfused, cudaStream_t st, Workspace** out) {
+int ws_zero(Workspace* w, cudaStream_t st) {
+    const uint64_t rows = (uint64_t)w->n * w->WB;
+    FBPT_CUDA_TRY(cudaMemsetAsync(w->visited, 0, rows * 8, st));
+    FBPT_CUDA_TRY(cudaMemsetAsync(w->next, 0, rows * 8, st));
+    FBPT_CUDA_TRY(cudaMemsetAsync(w->nocc, 0, (uint64_t)w->n * 8, st));
+    w->clean = true;
+    return FBPT_OK;
+}
+
+int ws_get(fbpt_graph* g, uint32_t WB, bool unfused, cudaStream_t st, Workspace** out) {
     Workspace* w = g->ws;
-    if (w && w->W == W && w->B == B && w->unfused == unfused) {
-        if (!w->clean) {
-            const uint64_t rows = (uint64_t)g->n * w->WB;
-            FBPT_CUDA_TRY(cudaMemsetAsync(w->visited, 0, rows * 8, st));
-            FBPT_CUDA_TRY(cudaMemsetAsync(w->next, 0, rows * 8, st));
-            FBPT_CUDA_TRY(cudaMemsetAsync(w->dirty, 0, w->nw * 8, st));
-            FBPT_CUDA_TRY(cudaMemsetAsync(w->touched, 0, (uint64_t)B * w->nw * 8, st));
-            w->clean = true;
-        }
+    if (w && w->WB == WB && w->unfused == unfused) {
+        if (!w->clean) FBPT_TRY(ws_zero(w, st));
         *out = w;
         return FBPT_OK;
     }
@@ -577,46 +805,42 @@ int ws_get(fbpt_graph* g, uint32_t W, uint32_t B, bool unfused, cudaStream_t st,
     }
     w = new Workspace();
     w->n = g->n;
-    w->W = W;
-    w->B = B;
-    w->WB = W * B;
+    w->WB = WB;
     w->unfused = unfused;
-    w->nw = (g->n + 63) / 64;
     const uint64_t n = g->n;
-    const uint64_t rows = n * w->WB;
+    const uint64_t rows = n * WB;
     w->pend_cap = n;
-    w->list_cap = unfused ? std::min<uint64_t>(n * (uint64_t)w->WB * 64, std::max<uint64_t>(16 * n, 1 << 20)) : n;
+    w->list_cap = unfused ? std::min<uint64_t>(n * 64ull * WB, std::max<uint64_t>(16 * n, 1 << 20)) : n;
     if (w->list_cap > kUnitMask) w->list_cap = kUnitMask;
     // groups of a row [rs, re) are at most (re - rs) / 4 + 2
-    const uint64_t max_groups = (g->m / 4 + 2 * n + 1) * (unfused ? 64ull * w->WB : 1ull);
-    w->tile_cap = std::min<uint64_t>(max_groups / kTileGroups + 2, (uint64_t)1 << 32);
+    const uint64_t max_groups = (g->m / 4 + 2 * n + 1) * (unfused ? 64ull * WB : 1ull);
+    w->chunk_cap = std::min<uint64_t>(max_groups / kChunk + 2, 0xFFFFFFFFull);
+    w->spill_cap = std::max<uint64_t>(1ull << 22, 4 * n);
     int rc = FBPT_OK;
     size_t& b = w->bytes;
     if (rc == FBPT_OK) rc = dalloc(&w->visited, rows, b);
     if (rc == FBPT_OK) rc = dalloc(&w->next, rows, b);
-    if (rc == FBPT_OK) rc = dalloc(&w->stage, w->pend_cap * w->WB, b);
-    if (rc == FBPT_OK) rc = dalloc(&w->dirty, w->nw, b);
-    if (rc == FBPT_OK) rc = dalloc(&w->touched, (uint64_t)B * w->nw, b);
-    if (rc == FBPT_OK) rc = dalloc(&w->tlist, (uint64_t)B * n, b);
+    if (rc == FBPT_OK) rc = dalloc(&w->nocc, n, b);
+    if (rc == FBPT_OK) rc = dalloc(&w->stage, w->pend_cap * WB, b);
     if (rc == FBPT_OK) rc = dalloc(&w->pend_v, w->pend_cap, b);
+    if (rc == FBPT_OK) rc = dalloc(&w->seg, 64ull * WB * kSegCap, b);
+    if (rc == FBPT_OK) rc = dalloc(&w->spill, 2 * w->spill_cap, b);
     if (rc == FBPT_OK) rc = dalloc(&w->list_v, w->list_cap, b);
     if (rc == FBPT_OK) rc = dalloc(&w->list_mrow, w->list_cap, b);
     if (rc == FBPT_OK && unfused) rc = dalloc(&w->list_only, w->list_cap, b);
+    if (rc == FBPT_OK) rc = dalloc(&w->list_rs, w->list_cap, b);
+    if (rc == FBPT_OK) rc = dalloc(&w->list_re, w->list_cap, b);
     if (rc == FBPT_OK) rc = dalloc(&w->list_g, w->list_cap, b);
     if (rc == FBPT_OK) rc = dalloc(&w->list_occ, w->list_cap, b);
-    if (rc == FBPT_OK) rc = dalloc(&w->tile_u0, w->tile_cap, b);
+    if (rc == FBPT_OK) rc = dalloc(&w->chunk_u0, w->chunk_cap, b);
     if (rc == FBPT_OK) rc = dalloc(&w->ctl, 1, b);
     if (rc == FBPT_OK && cudaMallocHost((void**)&w->ctl_host, sizeof(Ctl)) != cudaSuccess)
         rc = fail(FBPT_ENOMEM, "cudaMallocHost(ctl) failed");
+    if (rc == FBPT_OK) rc = ws_zero(w, st);
     if (rc != FBPT_OK) {
         ws_free(w);
         return rc;
     }
-    FBPT_CUDA_TRY(cudaMemsetAsync(w->visited, 0, rows * 8, st));
-    FBPT_CUDA_TRY(cudaMemsetAsync(w->next, 0, rows * 8, st));
-    FBPT_CUDA_TRY(cudaMemsetAsync(w->dirty, 0, w->nw * 8, st));
-    FBPT_CUDA_TRY(cudaMemsetAsync(w->touched, 0, (uint64_t)B * w->nw * 8, st));
-    w->clean = true;
     g->ws = w;
     *out = w;
     return FBPT_OK;
@@ -646,16 +870,19 @@ int sample_impl(fbpt_graph* g, uint64_t seed, uint64_t first_id, uint64_t S, con
     if (first_id + S < first_id) return fail(FBPT_EINVAL, "fbpt_sample: sample ids overflow");
     fbpt_opts o = {};
     if (opts) o = *opts;
-    uint32_t W = o.words ? o.words : 8;
+    const uint32_t W = o.words ? o.words : 8;
     if (W != 1 && W != 2 && W != 4 && W != 8) return fail(FBPT_EINVAL, "fbpt_sample: words must be 1, 2, 4 or 8");
-    uint32_t B = o.slots ? o.slots : kMaxWords / W;
+    const uint32_t B = o.slots ? o.slots : kMaxWords / W;
     if (B < 1 || B * W > kMaxWords) return fail(FBPT_EINVAL, "fbpt_sample: words * slots must be <= 64");
-    const uint64_t nbatches = (S + 64ull * W - 1) / (64ull * W);
-    if (B > nbatches) B = (uint32_t)nbatches;
+    uint32_t WB = W * B;
+    // never more lanes than samples (rounded up to whole words)
+    WB = (uint32_t)std::min<uint64_t>(WB, (S + 63) / 64);
     if (o.schedule != FBPT_SCHED_PUSH && o.schedule != FBPT_SCHED_HEURISTIC && o.schedule != FBPT_SCHED_LEARNED)
         return fail(FBPT_EUNSUPPORTED, "fbpt_sample: schedule not available");
-    if (o.launch != FBPT_LAUNCH_HOST && o.launch != FBPT_LAUNCH_GRAPH)
+    if (o.launch != FBPT_LAUNCH_HOST && o.launch != FBPT_LAUNCH_GRAPH && o.launch != FBPT_LAUNCH_PERSISTENT)
         return fail(FBPT_EINVAL, "fbpt_sample: bad launch mode");
+    if (o.refill != FBPT_REFILL_LANE && o.refill != FBPT_REFILL_BATCH)
+        return fail(FBPT_EINVAL, "fbpt_sample: bad refill mode");
     cudaStream_t st = o.stream ? (cudaStream_t)o.stream : g->stream;
     const uint32_t vbits = bits_for(g->n - 1);
     const uint32_t sbits = bits_for(S - 1);
@@ -667,7 +894,7 @@ int sample_impl(fbpt_graph* g, uint64_t seed, uint64_t first_id, uint64_t S, con
     cudaEventRecord(ev0, st);
 
     Workspace* ws = nullptr;
-    FBPT_TRY(ws_get(g, W, B, o.unfused != 0, st, &ws));
+    FBPT_TRY(ws_get(g, WB, o.unfused != 0, st, &ws));
 
     std::memset(out, 0, sizeof(*out));
     out->S = S;
@@ -686,33 +913,39 @@ int sample_impl(fbpt_graph* g, uint64_t seed, uint64_t first_id, uint64_t S, con
         FBPT_CUDA_TRY(cudaMallocAsync(&pairs, sizeof(uint64_t) * cap, st));
         FBPT_CUDA_TRY(cudaMemsetAsync(out->vcount, 0, sizeof(uint32_t) * g->n, st));
         std::memset(H, 0, sizeof(Ctl));
-        H->nbatches = nbatches;
+        H->S = S;
+        H->refill = o.refill == FBPT_REFILL_BATCH ? kRefillBatch : kRefillLane;
         H->pair_cap = cap;
-        H->exp_t0 = ~0ull;
-        const uint64_t rounds = nbatches / B + 2;
-        H->tick_limit = std::min<uint64_t>(rounds * ((uint64_t)g->n + 2), 1ull << 40);
+        for (int p = 0; p < 3; ++p) H->ph_t0[p] = ~0ull;
+        const uint64_t waves = S / (64ull * WB) + 2;
+        H->tick_limit = std::min<uint64_t>(waves * ((uint64_t)g->n + 2) + 16, 1ull << 40);
         FBPT_CUDA_TRY(cudaMemcpyAsync(ws->ctl, H, sizeof(Ctl), cudaMemcpyHostToDevice, st));
 
         Eng E = {};
-        E.n = g->n; E.W = W; E.B = B; E.WB = W * B; E.nw = ws->nw;
+        E.n = g->n; E.WB = WB;
         E.row_ptr = g->row_ptr; E.col = g->col; E.thr = g->thr;
         E.seed = seed; E.first_id = first_id; E.S = S;
-        E.visited = ws->visited; E.next = ws->next; E.stage = ws->stage; E.dirty = ws->dirty;
-        E.touched = ws->touched; E.tlist = ws->tlist; E.pend_v = ws->pend_v;
+        E.visited = ws->visited; E.next = ws->next; E.nocc = ws->nocc; E.stage = ws->stage;
+        E.pend_v = ws->pend_v; E.seg = ws->seg; E.spill = ws->spill;
         E.list_v = ws->list_v; E.list_mrow = ws->list_mrow; E.list_only = ws->list_only;
-        E.list_g = ws->list_g; E.list_occ = ws->list_occ; E.tile_u0 = ws->tile_u0;
-        E.pend_cap = ws->pend_cap; E.list_cap = ws->list_cap; E.tile_cap = ws->tile_cap;
+        E.list_rs = ws->list_rs; E.list_re = ws->list_re; E.list_g = ws->list_g; E.list_occ = ws->list_occ;
+        E.chunk_u0 = ws->chunk_u0;
+        E.pend_cap = ws->pend_cap; E.list_cap = ws->list_cap; E.chunk_cap = ws->chunk_cap;
+        E.spill_cap = ws->spill_cap;
         E.unfused = o.unfused ? 1u : 0u;
         E.vbits = vbits;
         E.ctl = ws->ctl;
         E.starts = out->starts; E.vcount = out->vcount; E.pairs = pairs;
         E.cond = 0;
+        E.spin_limit = o.spin_limit ? o.spin_limit : (1ull << 26);
         ws->clean = false;
         if (o.launch == FBPT_LAUNCH_GRAPH) {
             rc = run_graph(E, st);
+        } else if (o.launch == FBPT_LAUNCH_PERSISTENT) {
+            rc = run_persistent(E, st);
         } else {
             for (;;) {
-                rc = launch_tick(E, st);
+                rc = launch_level(E, st);
                 if (rc != FBPT_OK) break;
                 if (cudaMemcpyAsync(&H->running, &ws->ctl->running, sizeof(unsigned), cudaMemcpyDeviceToHost, st) !=
                         cudaSuccess ||
@@ -722,6 +955,7 @@ int sample_impl(fbpt_graph* g, uint64_t seed, uint64_t first_id, uint64_t S, con
                 }
                 if (!H->running) break;
             }
+            if (rc == FBPT_OK) rc = launch_final_sweep(E, st);
         }
         if (rc != FBPT_OK) break;
         if (cudaMemcpyAsync(H, ws->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
@@ -729,14 +963,18 @@ int sample_impl(fbpt_graph* g, uint64_t seed, uint64_t first_id, uint64_t S, con
             rc = fail(FBPT_ECUDA, std::string("sampling run: ") + cudaGetErrorString(cudaGetLastError()));
             break;
         }
+        if (H->error & kErrBarrierTimeout) {
+            rc = fail(FBPT_ETIMEOUT, "sampling run: a grid barrier wait gave up");
+            break;
+        }
         if (H->error) {
             rc = fail(FBPT_EDEVICE, "sampling run: device check failed (error bits " + std::to_string(H->error) + ")");
             break;
         }
-        ws->clean = true;  // every slot finished: kernels restored the zero state
+        ws->clean = true;  // every lane finished and was swept: the kernels restored the zero state
         if (H->pair_cursor <= cap) break;
         cap = H->pair_cursor + 1024;  // exact size is now known; run again
-        if (stats) stats->overflow_reruns += nbatches;
+        if (stats) stats->overflow_reruns += 1;
     }
     if (rc != FBPT_OK) {
         if (pairs) cudaFreeAsync(pairs, st);
@@ -749,7 +987,6 @@ int sample_impl(fbpt_graph* g, uint64_t seed, uint64_t first_id, uint64_t S, con
     }
     g->rr_hint = std::max(1.0, (double)total / (double)S);
     uint64_t* tmp = nullptr;
-    rc = FBPT_OK;
     if (cudaMallocAsync(&tmp, sizeof(uint64_t) * std::max<uint64_t>(total, 1), st) != cudaSuccess)
         rc = fail(FBPT_ENOMEM, "fbpt_sample: sort buffer");
     if (rc == FBPT_OK) rc = radix_sort_u64(pairs, tmp, total, vbits + sbits, st);
@@ -773,7 +1010,7 @@ int sample_impl(fbpt_graph* g, uint64_t seed, uint64_t first_id, uint64_t S, con
     cudaEventDestroy(ev1);
     if (stats) {
         stats->levels += H->tick;
-        stats->batches += H->st_batches;
+        stats->batches += (S + 64ull * WB - 1) / (64ull * WB);
         stats->push_levels += H->st_push;
         stats->units_expanded += H->st_units;
         stats->edge_accesses += H->st_edges;
@@ -782,7 +1019,9 @@ int sample_impl(fbpt_graph* g, uint64_t seed, uint64_t first_id, uint64_t S, con
         stats->rr_total += total;
         stats->mask_words += H->st_mask_words;
         stats->ms_total += ms;
-        stats->ms_expand += 1e-6 * (double)H->st_expand_ns;
+        stats->ms_expand += 1e-6 * (double)H->st_phase_ns[0];
+        stats->ms_commit += 1e-6 * (double)H->st_phase_ns[1];
+        stats->ms_sweep += 1e-6 * (double)H->st_phase_ns[2];
     }
     return FBPT_OK;
 }

@@ -8,19 +8,26 @@
 
 namespace fbpt {
 
-constexpr uint32_t kMaxWords = 64;      // words per vertex row (slots * W)
-constexpr uint32_t kMaxSlots = 64;
+constexpr uint32_t kMaxWords = 64;      // 64-bit colour words per vertex row
+constexpr uint32_t kMaxLanes = 64 * kMaxWords;
 constexpr uint32_t kUnitBits = 26;      // list allocation counter: units in the low 26 bits
 constexpr uint64_t kUnitMask = (1ull << kUnitBits) - 1;
-constexpr uint32_t kTileGroups = 1024;  // edge groups (4 edges each) per expand tile
-
-enum SlotState : uint32_t { kSlotIdle = 0, kSlotRunning = 1 };
+constexpr uint32_t kSegCap = 1024;      // RR entries a lane keeps in its own segment
+constexpr uint32_t kChunk = 32;         // 4-edge groups per expand chunk (one per lane)
+constexpr uint32_t kChunksPerGrab = 4;  // chunks a warp takes per atomic
 
 enum ErrorBits : uint32_t {
     kErrListOverflow = 1u,
-    kErrTileOverflow = 2u,
+    kErrChunkOverflow = 2u,
     kErrTickLimit = 4u,
     kErrPendOverflow = 8u,
+    kErrBarrierTimeout = 16u,
+    kErrSpillOverflow = 32u,
+};
+
+enum RefillMode : uint32_t {
+    kRefillLane = 0,   // a colour lane takes the next sample as soon as its traversal ends
+    kRefillBatch = 1,  // lanes are refilled only when every lane of the row has finished
 };
 
 // Device-resident control block of one sampling run.  Written and read only
@@ -29,51 +36,58 @@ struct Ctl {
     unsigned long long list_count;   // frontier units for the coming expand
     unsigned long long list_groups;  // their total 4-edge groups
     unsigned long long new_packed;   // commit's allocation counter (units | groups << 26)
-    unsigned long long active_mask;  // slots with a unit in the new list
-    unsigned int pend_count;         // vertices whose next mask changed this level
-    unsigned int tile_next;          // expand's dynamic tile counter
+    unsigned int pend_count;         // vertices whose next row changed this level
+    unsigned int chunk_next;         // expand's dynamic chunk counter
     unsigned int running;            // loop condition
-    unsigned int fin_count;
-    unsigned int init_count;
     unsigned int error;              // ErrorBits
+    unsigned int refill;             // RefillMode
+    unsigned int bar_count, bar_gen; // grid barrier of the persistent kernel
     unsigned long long tick, tick_limit;
-    unsigned long long next_batch, nbatches;
+    unsigned long long next_j, S;    // next sample index to hand out; samples in the run
     unsigned long long pair_cursor, pair_cap;
-    unsigned int slot_state[kMaxSlots];
-    unsigned int slot_ncol[kMaxSlots];
-    unsigned long long slot_base[kMaxSlots];  // sample id of colour 0 of the slot's batch
-    unsigned int tcount[kMaxSlots];           // touched vertices of the slot's batch
-    unsigned int fin_slot[kMaxSlots];
-    unsigned int fin_ncol[kMaxSlots];
-    unsigned long long fin_base[kMaxSlots];
-    unsigned int init_slot[kMaxSlots];
+    unsigned long long run_w[kMaxWords];   // lanes holding a sample
+    unsigned long long act_w[kMaxWords];   // lanes present in the new frontier
+    unsigned long long init_w[kMaxWords];  // lanes given a sample at the last schedule (init input)
+    unsigned int lane_j[kMaxLanes];        // sample index held by each lane
+    unsigned int lane_cnt[kMaxLanes];      // RR entries of the lane's current sample so far
+    unsigned int retired_j[kMaxLanes];     // sample index a finished lane held
+    // sweep input, written by the schedule: finished lanes and the prefix of
+    // their segment entry counts
+    unsigned int fin_count;
+    unsigned int fin_lane[kMaxLanes];
+    unsigned int fin_pre[kMaxLanes + 1];
+    unsigned long long fin_mask[kMaxWords]; // finished lanes as a bitmap (spill-log sweep)
+    unsigned int spill_cur, spill_sweep;   // spill log buffer commit appends to; sweep it this level
+    unsigned long long spill_len[2];
     // counters
-    unsigned long long st_edges, st_calls, st_units, st_cev, st_batches, st_push, st_pull;
-    // expand kernel time: first CTA start .. last CTA end of each launch (%globaltimer, ns)
-    unsigned long long exp_t0, exp_t1, st_expand_ns, st_mask_words;
+    unsigned long long st_edges, st_calls, st_units, st_cev, st_assigned, st_push, st_pull, st_mask_words;
+    // phase times: first CTA start .. last CTA end of each phase (%globaltimer, ns);
+    // index 0 expand, 1 commit, 2 sweep
+    unsigned long long ph_t0[3], ph_t1[3], st_phase_ns[3];
 };
 
 // Per-graph, per-shape working memory.  Every array is all-zero between runs
 // (the kernels restore what they dirty), except the scratch lists.
 struct Workspace {
     uint32_t n = 0;
-    uint32_t W = 0, B = 0, WB = 0;
-    uint64_t nw = 0;              // 64-bit words of an n-bit bitmap
-    uint64_t* visited = nullptr;  // n * WB
-    uint64_t* next = nullptr;     // n * WB
+    uint32_t WB = 0;
+    bool unfused = false;
+    uint64_t* visited = nullptr;  // n * WB: colours that reached v
+    uint64_t* next = nullptr;     // n * WB: colours reaching v at the current level
+    uint64_t* nocc = nullptr;     // n: bit i set iff next[v][i] != 0 (and v is pending)
     uint64_t* stage = nullptr;    // pend_cap * WB: new frontier masks by pend index
-    uint64_t* dirty = nullptr;    // nw
-    uint64_t* touched = nullptr;  // B * nw
-    uint32_t* tlist = nullptr;    // B * n
     uint32_t* pend_v = nullptr;   // pend_cap
+    uint32_t* seg = nullptr;      // 64 * WB * kSegCap: each lane's RR vertices
+    uint64_t* spill = nullptr;    // 2 * spill_cap: (lane << 32 | vertex) beyond a full segment
     uint32_t* list_v = nullptr;   // list_cap
     uint32_t* list_mrow = nullptr;
     uint32_t* list_only = nullptr;
+    uint64_t* list_rs = nullptr;
+    uint64_t* list_re = nullptr;
     uint64_t* list_g = nullptr;
     uint64_t* list_occ = nullptr;
-    uint32_t* tile_u0 = nullptr;  // tile_cap
-    uint64_t pend_cap = 0, list_cap = 0, tile_cap = 0;
-    bool unfused = false;
+    uint32_t* chunk_u0 = nullptr; // chunk_cap
+    uint64_t pend_cap = 0, list_cap = 0, chunk_cap = 0, spill_cap = 0;
     Ctl* ctl = nullptr;
     Ctl* ctl_host = nullptr;      // pinned mirror
     bool clean = false;
@@ -82,26 +96,27 @@ struct Workspace {
 
 // Kernel parameters of one run (passed by value).
 struct Eng {
-    uint32_t n, W, B, WB;
-    uint64_t nw;
+    uint32_t n, WB;
     const uint64_t* row_ptr;
     const uint32_t* col;
     const uint32_t* thr;
     uint64_t seed, first_id, S;
     uint64_t* visited;
     uint64_t* next;
+    uint64_t* nocc;
     uint64_t* stage;
-    uint64_t* dirty;
-    uint64_t* touched;
-    uint32_t* tlist;
     uint32_t* pend_v;
+    uint32_t* seg;
+    uint64_t* spill;
     uint32_t* list_v;
     uint32_t* list_mrow;
     uint32_t* list_only;
+    uint64_t* list_rs;
+    uint64_t* list_re;
     uint64_t* list_g;
     uint64_t* list_occ;
-    uint32_t* tile_u0;
-    uint64_t pend_cap, list_cap, tile_cap;
+    uint32_t* chunk_u0;
+    uint64_t pend_cap, list_cap, chunk_cap, spill_cap;
     uint32_t unfused;
     uint32_t vbits;               // bits of a vertex id in a pair key
     Ctl* ctl;
@@ -109,6 +124,7 @@ struct Eng {
     uint32_t* vcount;             // n
     uint64_t* pairs;              // pair_cap: (sample index << vbits) | vertex
     unsigned long long cond;      // cudaGraphConditionalHandle (0 = host-driven loop)
+    unsigned long long spin_limit;  // bounded waits of the persistent kernel's grid barrier
 };
 
 }  // namespace fbpt

@@ -55,7 +55,7 @@ def test_device_starts_match_oracle(fbpt, n):
 
 # ---- the ER 1k workload (1,024 vertices, 8,192 edges, p = 0.1, 64 samples, k = 4) -----------
 
-@pytest.mark.parametrize("launch", ["host", "graph"])
+@pytest.mark.parametrize("launch", ["host", "graph", "persistent"])
 @pytest.mark.parametrize("words,slots", [(1, 1), (1, 0), (2, 0), (8, 1)])
 def test_er1k_bit_exact(fbpt, er_workload, launch, words, slots):
     w = er_workload
@@ -98,16 +98,31 @@ def rmat13_wc():
     return synth.rmat_wc(13)
 
 
+@pytest.mark.parametrize("refill", ["lane", "batch"])
 @pytest.mark.parametrize("words,slots,first,S", [
     (1, 3, 0, 1000), (2, 0, 3, 1337), (4, 2, 2**33 + 1, 700), (8, 8, 17, 4100), (8, 1, 0, 1)])
-def test_rmat_uniform_bit_exact(fbpt, rmat12, words, slots, first, S):
+def test_rmat_uniform_bit_exact(fbpt, rmat12, words, slots, first, S, refill):
     g = rmat12
     dg = fbpt.Graph.from_synth(g)
-    rr = fbpt.sample(dg, SEED, first, S, words=words, slots=slots)
+    rr = fbpt.sample(dg, SEED, first, S, words=words, slots=slots, refill=refill)
     assert_same(rr, oracle.rr_sets(g, SEED, first, S), g)
 
 
-@pytest.mark.parametrize("launch", ["host", "graph"])
+@pytest.mark.parametrize("launch", ["host", "graph", "persistent"])
+def test_plain_batches_equal_lane_refill(fbpt, rmat12, launch):
+    """The plain fused algorithm (one group of 64 colours at a time, run to
+    completion) and lane refill give the same bits."""
+    g = rmat12
+    dg = fbpt.Graph.from_synth(g)
+    ref = oracle.rr_sets(g, SEED, 5, 900)
+    plain = fbpt.sample(dg, SEED, 5, 900, words=1, slots=1, refill="batch", launch=launch)
+    lanes = fbpt.sample(dg, SEED, 5, 900, words=1, slots=1, refill="lane", launch=launch)
+    assert_same(plain, ref, g)
+    assert_same(lanes, ref, g)
+    assert lanes.stats.levels <= plain.stats.levels
+
+
+@pytest.mark.parametrize("launch", ["host", "graph", "persistent"])
 def test_rmat_wc_bit_exact(fbpt, rmat13_wc, launch):
     g = rmat13_wc
     dg = fbpt.Graph.from_synth(g)
