@@ -91,6 +91,23 @@ enum fbpt_refill {
                               algorithm with 64 * words * slots colours per group */
 };
 
+/* One row per level of a sampling run, filled when fbpt_opts.trace is set.
+ * The schedule policy is trained on these rows (features of a level and the
+ * time each phase took). */
+typedef struct fbpt_trace_row {
+    uint64_t level;          /* level index within the run */
+    uint64_t units;          /* frontier units expanded at this level */
+    uint64_t groups;         /* their 4-edge groups (expand work items) */
+    uint64_t colours;        /* colour bits carried by the units */
+    uint64_t pending;        /* vertices whose next row changed (commit work items) */
+    uint64_t active_lanes;   /* lanes still traversing after this level */
+    uint64_t finished_lanes; /* lanes whose sample ended at this level */
+    uint64_t started_lanes;  /* lanes given a new sample at this level */
+    uint64_t expand_ns, commit_ns, sweep_ns;  /* device time of each phase (%globaltimer) */
+    uint32_t direction;      /* 0 push, 1 pull */
+    uint32_t reserved;
+} fbpt_trace_row;
+
 typedef struct fbpt_graph fbpt_graph;
 typedef struct fbpt_policy fbpt_policy;
 
@@ -104,11 +121,14 @@ typedef struct fbpt_opts {
     uint32_t unfused;    /* 1 = each colour expands its own copy of every edge (no fusing);
                             output is identical, only the work differs */
     uint32_t refill;     /* enum fbpt_refill */
-    uint32_t record_trace; /* 1 = keep per-level features/timings (fbpt_trace_*) */
+    uint32_t reserved0;
     const fbpt_policy* policy; /* used by FBPT_SCHED_LEARNED; NULL = built-in heuristic */
     void* stream;        /* cudaStream_t */
     uint64_t spin_limit; /* FBPT_LAUNCH_PERSISTENT: polls before a grid-barrier wait gives up
                             (0 = default, about a few seconds) */
+    fbpt_trace_row* trace; /* host array of trace_cap rows, or NULL; levels beyond trace_cap
+                              are not recorded */
+    uint64_t trace_cap;
 } fbpt_opts;
 
 /* RR sets as CSR in library-owned device memory (free with fbpt_rrsets_free). */
@@ -135,6 +155,7 @@ typedef struct fbpt_stats {
     uint64_t rr_total;            /* sum of RR set sizes */
     uint64_t overflow_reruns;     /* batches re-run after the output pool grew */
     uint64_t mask_words;          /* non-zero 64-colour mask words of expanded frontier units */
+    uint64_t trace_rows;          /* rows written to fbpt_opts.trace */
     double ms_total;              /* time of the call on its stream (CUDA events) */
     double ms_expand;             /* device time of the expand phase: per level, first CTA start
                                      to last CTA end (%globaltimer), summed */

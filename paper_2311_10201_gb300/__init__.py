@@ -33,8 +33,9 @@ U32P = ctypes.POINTER(ctypes.c_uint32)
 class Opts(ctypes.Structure):
     _fields_ = [("words", ctypes.c_uint32), ("slots", ctypes.c_uint32), ("schedule", ctypes.c_uint32),
                 ("launch", ctypes.c_uint32), ("unfused", ctypes.c_uint32), ("refill", ctypes.c_uint32),
-                ("record_trace", ctypes.c_uint32),
-                ("policy", ctypes.c_void_p), ("stream", ctypes.c_void_p), ("spin_limit", ctypes.c_uint64)]
+                ("reserved0", ctypes.c_uint32),
+                ("policy", ctypes.c_void_p), ("stream", ctypes.c_void_p), ("spin_limit", ctypes.c_uint64),
+                ("trace", ctypes.c_void_p), ("trace_cap", ctypes.c_uint64)]
 
 
 class RRSetsC(ctypes.Structure):
@@ -46,12 +47,18 @@ class RRSetsC(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_uint64) for k in
                 ("levels", "batches", "push_levels", "pull_levels", "units_expanded", "edge_accesses",
-                 "philox_calls", "colour_edge_visits", "rr_total", "overflow_reruns", "mask_words")] + \
+                 "philox_calls", "colour_edge_visits", "rr_total", "overflow_reruns", "mask_words", "trace_rows")] + \
                [("ms_total", ctypes.c_double), ("ms_expand", ctypes.c_double), ("ms_commit", ctypes.c_double),
                 ("ms_sweep", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+TRACE_DTYPE = np.dtype([(k, np.uint64) for k in
+                        ("level", "units", "groups", "colours", "pending", "active_lanes", "finished_lanes",
+                         "started_lanes", "expand_ns", "commit_ns", "sweep_ns")] +
+                       [("direction", np.uint32), ("reserved", np.uint32)])
 
 
 class FbptError(RuntimeError):
@@ -226,13 +233,21 @@ def make_opts(words=0, slots=0, schedule="push", launch="persistent", unfused=Fa
     return o
 
 
-def sample(g: Graph, seed: int, first_id: int, S: int, stream=None, **kw) -> RRSets:
-    """RR sets of samples first_id .. first_id+S-1 (fbpt_sample)."""
+def sample(g: Graph, seed: int, first_id: int, S: int, stream=None, trace_cap: int = 0, **kw) -> RRSets:
+    """RR sets of samples first_id .. first_id+S-1 (fbpt_sample).  With
+    trace_cap > 0 the per-level trace is returned as rr.trace."""
     o = make_opts(stream=_stream_handle(stream) if stream is not None else g.stream, **kw)
+    trace = None
+    if trace_cap:
+        trace = np.zeros(trace_cap, TRACE_DTYPE)
+        o.trace = trace.ctypes.data
+        o.trace_cap = trace_cap
     c = RRSetsC()
     st = Stats()
     _check(lib().fbpt_sample(g._h, seed, first_id, S, ctypes.byref(o), ctypes.byref(c), ctypes.byref(st)))
-    return RRSets(c, st)
+    rr = RRSets(c, st)
+    rr.trace = trace[:st.trace_rows] if trace is not None else None
+    return rr
 
 
 def sample_batched(graphs, seeds, first_ids, Ss, stream=None, **kw):

@@ -49,13 +49,24 @@ __device__ __forceinline__ uint64_t row_groups(uint64_t rs, uint64_t re) {
 template <typename T>
 __device__ __forceinline__ T L2(const T* p) { return __ldcg(p); }
 
+// Commit scratch of one warp: its 32 pending vertices and what their words add.
+struct CommitWarp {
+    uint64_t m[32];                 // words of next[w] that changed this level
+    uint32_t w[32];
+    uint32_t start[32];             // first (vertex, word) item of each vertex
+    uint32_t occ_lo[32], occ_hi[32];
+    uint32_t bits[32];
+    uint32_t he[32];                // vertex has in-edges
+};
+
 struct Smem {
     uint32_t lane[kMaxLanes + 1];   // expand: sample index per lane; sweep, schedule: entry prefixes
-    uint64_t act[kMaxWords];        // commit: lanes seen in this CTA's new units
+    uint32_t act[2 * kMaxWords];    // commit: lanes seen in this CTA's new units (32-bit halves)
+    CommitWarp cw[kThreads / 32];   // commit
     uint64_t fin[kMaxWords];        // sweep: finished lanes (spill-log sweep)
     uint32_t cnt[kMaxWords + 1];    // schedule: per-word counts, then their prefix
     uint32_t tsum[kThreads + 1];    // schedule: per-thread sums of the block scan
-    uint32_t last, abort;
+    uint32_t last, abort, nstill;
 };
 
 __device__ __forceinline__ void phase_begin(Ctl* ctl, int p) {
@@ -283,7 +294,8 @@ __device__ void dev_expand(const Eng& E, Smem& sm) {
 // ---- commit -------------------------------------------------------------------------
 
 __device__ __forceinline__ void write_unit(const Eng& E, uint64_t pos, uint32_t w, uint32_t mrow, uint64_t occ,
-                                           uint32_t only, uint64_t rs, uint64_t re, uint64_t gbeg, uint64_t ng) {
+                                           uint32_t only, uint64_t rs, uint64_t re, uint64_t gbeg, uint64_t ng,
+                                           bool chunks) {
     E.list_v[pos] = w;
     E.list_mrow[pos] = mrow;
     E.list_occ[pos] = occ;
@@ -291,6 +303,7 @@ __device__ __forceinline__ void write_unit(const Eng& E, uint64_t pos, uint32_t 
     E.list_re[pos] = re;
     E.list_g[pos] = gbeg;
     if (E.unfused) E.list_only[pos] = only;
+    if (!chunks) return;
     // chunks whose first group falls inside this unit start their search here
     const uint64_t end = gbeg + ng;
     for (uint64_t c = (gbeg + kChunk - 1) / kChunk; c * kChunk < end; ++c) {
@@ -299,14 +312,22 @@ __device__ __forceinline__ void write_unit(const Eng& E, uint64_t pos, uint32_t 
     }
 }
 
+// Position of the r-th (0-based) set bit of m.
+__device__ __forceinline__ uint32_t nth_bit64(uint64_t m, uint32_t r) {
+    const uint32_t lo = (uint32_t)m, pl = __popc(lo);
+    return r < pl ? __fns(lo, 0, (int)r + 1) : 32u + __fns((uint32_t)(m >> 32), 0, (int)(r - pl) + 1);
+}
+
 // For every pending vertex w and every word i with next[w][i] != 0:
-// nx = next[w][i] & ~visited[w][i]; next[w][i] = 0; visited[w][i] |= nx.
-// Non-empty rows become frontier units (if w has in-edges); w joins word i's
-// touched list when it is the first colour of that word to reach w.
+// nx = next[w][i] & ~visited[w][i]; next[w][i] = 0; visited[w][i] |= nx; each
+// new colour appends w to its lane's entries.  The (vertex, word) items of a
+// warp's 32 vertices are spread over its lanes, so a hub reached by many
+// colours at once is not left to one thread.  Non-empty rows become frontier
+// units (if w has in-edges).
 __device__ void dev_commit(const Eng& E, Smem& sm) {
     Ctl* ctl = E.ctl;
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < E.WB; i += blockDim.x) sm.act[i] = 0;
+    for (uint32_t i = threadIdx.x; i < 2 * E.WB; i += blockDim.x) sm.act[i] = 0;
     __syncthreads();
     const uint32_t P = (uint32_t)min((uint64_t)L2(&ctl->pend_count), E.pend_cap);
     if (P) phase_begin(ctl, 1);
@@ -314,83 +335,132 @@ __device__ void dev_commit(const Eng& E, Smem& sm) {
     const uint32_t lane = lane_id();
     const uint64_t wid = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarp = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    uint64_t mwords = 0;
+    CommitWarp& cw = sm.cw[threadIdx.x >> 5];
+    uint64_t mwords = 0, ncol = 0;
     for (uint64_t base = wid * 32; base < P; base += nwarp * 32) {
         const uint64_t idx = base + lane;
         const bool ok = idx < P;
-        uint32_t w = 0, bits = 0;
-        uint64_t occ = 0, rs = 0, re = 0;
+        uint32_t w = 0;
+        uint64_t m = 0, rs = 0, re = 0;
         if (ok) {
             w = L2(&E.pend_v[idx]);
-            uint64_t m = L2(&E.nocc[w]);
+            m = L2(&E.nocc[w]);
             E.nocc[w] = 0;
             rs = __ldg(&E.row_ptr[w]);
             re = __ldg(&E.row_ptr[w + 1]);
-            const bool has_edges = re > rs;
-            while (m) {
-                const uint32_t i = __ffsll((long long)m) - 1;
-                m &= m - 1;
-                const uint64_t rowi = (uint64_t)w * E.WB + i;
-                uint64_t nx = L2(&E.next[rowi]);
-                E.next[rowi] = 0;
-                const uint64_t vis = L2(&E.visited[rowi]);
-                nx &= ~vis;
-                if (!nx) continue;
-                E.visited[rowi] = vis | nx;
-                E.stage[idx * E.WB + i] = nx;
-                occ |= 1ull << i;
-                bits += __popcll(nx);
-                // each new colour adds w to its lane's RR entries
-                uint64_t nb = nx;
-                while (nb) {
-                    const uint32_t c = __ffsll((long long)nb) - 1;
-                    nb &= nb - 1;
-                    const uint32_t l = (i << 6) + c;
-                    const uint32_t pos = atomicAdd(&ctl->lane_cnt[l], 1u);
-                    if (pos < kSegCap) {
-                        E.seg[(uint64_t)l * kSegCap + pos] = w;
-                    } else {
-                        const uint64_t sp = atomicAdd(&ctl->spill_len[spill_cur], 1ull);
-                        if (sp < E.spill_cap) E.spill[(uint64_t)spill_cur * E.spill_cap + sp] = ((uint64_t)l << 32) | w;
-                        else atomicOr(&ctl->error, (unsigned)kErrSpillOverflow);
-                    }
+        }
+        const uint32_t ni = __popcll(m);
+        const uint32_t incl = warp_incl_scan(ni);
+        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        cw.m[lane] = m;
+        cw.w[lane] = w;
+        cw.start[lane] = incl - ni;
+        cw.occ_lo[lane] = 0;
+        cw.occ_hi[lane] = 0;
+        cw.bits[lane] = 0;
+        cw.he[lane] = re > rs;
+        __syncwarp();
+        for (uint32_t t = lane; t < total; t += 32) {
+            uint32_t o = 0;  // the vertex owning item t: largest o with start[o] <= t
+#pragma unroll
+            for (uint32_t step = 16; step > 0; step >>= 1)
+                if (cw.start[o + step] <= t) o += step;
+            const uint32_t i = nth_bit64(cw.m[o], t - cw.start[o]);
+            const uint32_t wv = cw.w[o];
+            const uint64_t rowi = (uint64_t)wv * E.WB + i;
+            uint64_t nx = L2(&E.next[rowi]);
+            E.next[rowi] = 0;
+            const uint64_t vis = L2(&E.visited[rowi]);
+            nx &= ~vis;
+            if (!nx) continue;
+            E.visited[rowi] = vis | nx;
+            E.stage[(base + o) * E.WB + i] = nx;
+            if (i < 32) atomicOr(&cw.occ_lo[o], 1u << i);
+            else atomicOr(&cw.occ_hi[o], 1u << (i - 32));
+            atomicAdd(&cw.bits[o], (uint32_t)__popcll(nx));
+            if (cw.he[o]) {
+                if ((uint32_t)nx) atomicOr(&sm.act[2 * i], (uint32_t)nx);
+                if (nx >> 32) atomicOr(&sm.act[2 * i + 1], (uint32_t)(nx >> 32));
+            }
+            uint64_t nb = nx;
+            while (nb) {
+                const uint32_t c = __ffsll((long long)nb) - 1;
+                nb &= nb - 1;
+                const uint32_t l = (i << 6) + c;
+                const uint32_t pos = atomicAdd(&ctl->lane_cnt[l], 1u);
+                if (pos < kSegCap) {
+                    E.seg[(uint64_t)l * kSegCap + pos] = wv;
+                } else {
+                    const uint64_t sp = atomicAdd(&ctl->spill_len[spill_cur], 1ull);
+                    if (sp < E.spill_cap) E.spill[(uint64_t)spill_cur * E.spill_cap + sp] = ((uint64_t)l << 32) | wv;
+                    else atomicOr(&ctl->error, (unsigned)kErrSpillOverflow);
                 }
-                if (has_edges) atomicOr((unsigned long long*)&sm.act[i], (unsigned long long)nx);
             }
         }
+        __syncwarp();
+        const uint64_t occ = ((uint64_t)cw.occ_hi[lane] << 32) | cw.occ_lo[lane];
+        const uint32_t bits = cw.bits[lane];
+        __syncwarp();
         const uint64_t ng = occ ? row_groups(rs, re) : 0;
         const uint64_t units = ng ? (E.unfused ? bits : 1u) : 0u;
         mwords += units ? (E.unfused ? units : (uint64_t)__popcll(occ)) : 0;
+        ncol += units ? bits : 0;
         const unsigned long long req = (unsigned long long)((units * ng) << kUnitBits) | units;
         const unsigned long long got = warp_alloc<unsigned long long>(&ctl->new_packed, req);
-        if (units) {
-            uint64_t pos = got & kUnitMask;
-            uint64_t gbeg = got >> kUnitBits;
-            if (pos + units > E.list_cap) {
-                atomicOr(&ctl->error, (unsigned)kErrListOverflow);
-            } else if (!E.unfused) {
-                write_unit(E, pos, w, (uint32_t)idx, occ, 0u, rs, re, gbeg, ng);
-            } else {
-                uint64_t ws = occ;
-                while (ws) {
-                    const uint32_t i = __ffsll((long long)ws) - 1;
-                    ws &= ws - 1;
-                    uint64_t x = E.stage[idx * E.WB + i];
-                    while (x) {
-                        const uint32_t c = __ffsll((long long)x) - 1;
-                        x &= x - 1;
-                        write_unit(E, pos++, w, (uint32_t)idx, 1ull << i, i * 64u + c + 1u, rs, re, gbeg, ng);
-                        gbeg += ng;
-                    }
+        const uint64_t pos0 = got & kUnitMask;
+        const uint64_t gbeg0 = got >> kUnitBits;
+        const bool fits = units && pos0 + units <= E.list_cap;
+        if (units && !fits) atomicOr(&ctl->error, (unsigned)kErrListOverflow);
+        if (fits && !E.unfused) {
+            write_unit(E, pos0, w, (uint32_t)idx, occ, 0u, rs, re, gbeg0, ng, false);
+        } else if (fits) {
+            uint64_t pos = pos0, gbeg = gbeg0;
+            uint64_t ws = occ;
+            while (ws) {
+                const uint32_t i = __ffsll((long long)ws) - 1;
+                ws &= ws - 1;
+                uint64_t x = E.stage[idx * E.WB + i];
+                while (x) {
+                    const uint32_t c = __ffsll((long long)x) - 1;
+                    x &= x - 1;
+                    write_unit(E, pos++, w, (uint32_t)idx, 1ull << i, i * 64u + c + 1u, rs, re, gbeg, ng, true);
+                    gbeg += ng;
                 }
             }
         }
+        // chunk map of the fused units: every chunk whose first group lies in a
+        // unit points at it; the writes of the warp's units are spread over its lanes
+        uint32_t c0 = 0, nck = 0;
+        if (fits && !E.unfused) {
+            c0 = (uint32_t)((gbeg0 + kChunk - 1) / kChunk);
+            nck = (uint32_t)((gbeg0 + ng + kChunk - 1) / kChunk) - c0;
+        }
+        const uint32_t cincl = warp_incl_scan(nck);
+        const uint32_t ctot = __shfl_sync(0xffffffffu, cincl, 31);
+        cw.start[lane] = cincl - nck;
+        cw.w[lane] = (uint32_t)pos0;
+        cw.occ_lo[lane] = c0;
+        __syncwarp();
+        for (uint32_t t = lane; t < ctot; t += 32) {
+            uint32_t o = 0;
+#pragma unroll
+            for (uint32_t step = 16; step > 0; step >>= 1)
+                if (cw.start[o + step] <= t) o += step;
+            const uint64_t c = (uint64_t)cw.occ_lo[o] + (t - cw.start[o]);
+            if (c < E.chunk_cap) E.chunk_u0[c] = cw.w[o];
+            else atomicOr(&ctl->error, (unsigned)kErrChunkOverflow);
+        }
+        __syncwarp();
     }
     mwords = warp_sum(mwords);
+    ncol = warp_sum(ncol);
     if (lane == 0 && mwords) atomicAdd(&ctl->st_mask_words, (unsigned long long)mwords);
+    if (lane == 0 && ncol) atomicAdd(&ctl->new_colours, (unsigned long long)ncol);
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < E.WB; i += blockDim.x)
-        if (sm.act[i]) atomicOr(&ctl->act_w[i], (unsigned long long)sm.act[i]);
+    for (uint32_t i = threadIdx.x; i < E.WB; i += blockDim.x) {
+        const unsigned long long a = ((unsigned long long)sm.act[2 * i + 1] << 32) | sm.act[2 * i];
+        if (a) atomicOr(&ctl->act_w[i], a);
+    }
     if (P) phase_end(ctl, 1);
 }
 
@@ -414,16 +484,19 @@ __device__ void dev_schedule(const Eng& E, Smem& sm) {
         fin = run & ~act;
         sm.cnt[i] = __popcll(fin);
     }
+    if (mine) sm.tsum[i] = __popcll(still);
     const bool any_still = __syncthreads_or(still != 0);
     // finished lanes, word by word: base index of each word's finished lanes
     if (threadIdx.x == 0) {
-        uint32_t acc = 0;
+        uint32_t acc = 0, ns = 0;
         for (uint32_t w = 0; w < E.WB; ++w) {
             const uint32_t c = sm.cnt[w];
             sm.cnt[w] = acc;
             acc += c;
+            ns += sm.tsum[w];
         }
         sm.cnt[E.WB] = acc;
+        sm.nstill = ns;
     }
     __syncthreads();
     const uint32_t F = sm.cnt[E.WB];
@@ -521,6 +594,27 @@ __device__ void dev_schedule(const Eng& E, Smem& sm) {
         }
         ctl->spill_sweep = any_spill ? 1u : 0u;
         const uint64_t assigned = min((uint64_t)sm.cnt[E.WB], avail);
+        const unsigned long long tick = L2(&ctl->tick);
+        if (E.trace && tick < E.trace_cap) {
+            fbpt_trace_row& row = E.trace[tick];
+            row.level = tick;
+            row.units = L2(&ctl->list_count);
+            row.groups = L2(&ctl->list_groups);
+            row.colours = L2(&ctl->list_colours);
+            row.pending = L2(&ctl->pend_count);
+            row.active_lanes = sm.nstill;
+            row.finished_lanes = F;
+            row.started_lanes = assigned;
+            uint64_t* pt[3] = {&row.expand_ns, &row.commit_ns, &row.sweep_ns};
+            for (int p = 0; p < 3; ++p) {
+                const unsigned long long t0 = L2(&ctl->ph_t0[p]), t1 = L2(&ctl->ph_t1[p]);
+                *pt[p] = t1 > t0 ? t1 - t0 : 0;
+            }
+            row.direction = 0;
+            row.reserved = 0;
+        }
+        ctl->list_colours = err ? 0 : L2(&ctl->new_colours);
+        ctl->new_colours = 0;
         ctl->next_j = base_j + assigned;
         ctl->st_assigned += assigned;
         const unsigned long long np = L2(&ctl->new_packed);
@@ -537,10 +631,9 @@ __device__ void dev_schedule(const Eng& E, Smem& sm) {
         ctl->new_packed = 0;
         ctl->chunk_next = 0;
         ctl->pend_count = 0;
-        const unsigned long long tick = L2(&ctl->tick) + 1;
-        ctl->tick = tick;
+        ctl->tick = tick + 1;
         uint32_t run = any_run ? 1u : 0u;
-        if (tick > L2(&ctl->tick_limit)) {
+        if (tick + 1 > L2(&ctl->tick_limit)) {
             atomicOr(&ctl->error, (unsigned)kErrTickLimit);
             run = 0;
         }
@@ -906,6 +999,9 @@ int sample_impl(fbpt_graph* g, uint64_t seed, uint64_t first_id, uint64_t S, con
 
     uint64_t cap = (uint64_t)(g->rr_hint * 1.25 * (double)S) + 4096;
     uint64_t* pairs = nullptr;
+    fbpt_trace_row* dtrace = nullptr;
+    if (o.trace && o.trace_cap)
+        FBPT_CUDA_TRY(cudaMallocAsync(&dtrace, sizeof(fbpt_trace_row) * o.trace_cap, st));
     Ctl* H = ws->ctl_host;
     int rc = FBPT_OK;
     for (int attempt = 0; attempt < 3; ++attempt) {
@@ -938,6 +1034,8 @@ int sample_impl(fbpt_graph* g, uint64_t seed, uint64_t first_id, uint64_t S, con
         E.starts = out->starts; E.vcount = out->vcount; E.pairs = pairs;
         E.cond = 0;
         E.spin_limit = o.spin_limit ? o.spin_limit : (1ull << 26);
+        E.trace = dtrace;
+        E.trace_cap = dtrace ? o.trace_cap : 0;
         ws->clean = false;
         if (o.launch == FBPT_LAUNCH_GRAPH) {
             rc = run_graph(E, st);
@@ -975,6 +1073,17 @@ int sample_impl(fbpt_graph* g, uint64_t seed, uint64_t first_id, uint64_t S, con
         if (H->pair_cursor <= cap) break;
         cap = H->pair_cursor + 1024;  // exact size is now known; run again
         if (stats) stats->overflow_reruns += 1;
+    }
+    if (dtrace) {
+        if (rc == FBPT_OK) {
+            const uint64_t rows = std::min<uint64_t>(H->tick, o.trace_cap);
+            if (cudaMemcpyAsync(o.trace, dtrace, sizeof(fbpt_trace_row) * rows, cudaMemcpyDeviceToHost, st) !=
+                    cudaSuccess ||
+                cudaStreamSynchronize(st) != cudaSuccess)
+                rc = fail(FBPT_ECUDA, "fbpt_sample: trace copy failed");
+            if (stats) stats->trace_rows = rows;
+        }
+        cudaFreeAsync(dtrace, st);
     }
     if (rc != FBPT_OK) {
         if (pairs) cudaFreeAsync(pairs, st);

@@ -61,6 +61,7 @@ struct Ctl {
     unsigned long long spill_len[2];
     // counters
     unsigned long long st_edges, st_calls, st_units, st_cev, st_assigned, st_push, st_pull, st_mask_words;
+    unsigned long long new_colours, list_colours;  // colour bits of the new / current frontier units
     // phase times: first CTA start .. last CTA end of each phase (%globaltimer, ns);
     // index 0 expand, 1 commit, 2 sweep
     unsigned long long ph_t0[3], ph_t1[3], st_phase_ns[3];
@@ -123,6 +124,8 @@ struct Eng {
     uint32_t* starts;             // S
     uint32_t* vcount;             // n
     uint64_t* pairs;              // pair_cap: (sample index << vbits) | vertex
+    fbpt_trace_row* trace;        // device copy of the per-level trace (NULL = off)
+    uint64_t trace_cap;
     unsigned long long cond;      // cudaGraphConditionalHandle (0 = host-driven loop)
     unsigned long long spin_limit;  // bounded waits of the persistent kernel's grid barrier
 };
