@@ -39,6 +39,12 @@ namespace fbpt {
 namespace {
 
 constexpr int kThreads = 256;
+#ifndef FBPT_EXPAND_ILP
+#define FBPT_EXPAND_ILP 1   // chunks a warp works on at once in the expand
+#endif
+#ifndef FBPT_EXPAND_MINB
+#define FBPT_EXPAND_MINB 3  // resident CTAs per SM the expand kernel is compiled for
+#endif
 
 __device__ __forceinline__ uint64_t row_groups(uint64_t rs, uint64_t re) {
     return re > rs ? ((re - 1) >> 2) - (rs >> 2) + 1 : 0;
@@ -189,64 +195,109 @@ __device__ void dev_init(const Eng& E) {
 // One 4-edge group of frontier unit u: edges 4q .. 4q+3 of the in-row [rs, re)
 // of its vertex, q = rs/4 + j.  For each colour of the unit one Philox call
 // decides all four edges (Listing 1's per-colour liveness draw); live colours
-// are ORed into next[w] (Listing 1's fusing update).
-__device__ __forceinline__ void expand_group(const Eng& E, const Smem& sm, uint32_t u, uint64_t j,
-                                             uint64_t& n_edges, uint64_t& n_calls) {
-    const uint64_t occ = L2(&E.list_occ[u]);
-    const uint32_t mrow = L2(&E.list_mrow[u]);
+// are ORed into next[w] (Listing 1's fusing update).  Loading and drawing are
+// split so that a warp can issue the loads of two chunks before drawing.
+struct Grp {
+    uint4 c4;          // sources of the four edges
+    uint4 tm;          // live iff draw <= tm (thr - 1; 0xFFFFFFFF for always-live edges)
+    uint64_t q, occ;
+    uint32_t mrow, only;
+    uint32_t valid;    // edges of the row with a non-zero threshold (bits 0..3)
+    uint32_t sure;     // of those, edges that are always live
+};
+
+__device__ __forceinline__ bool grp_load(const Eng& E, uint32_t u, uint64_t j, Grp& G, uint64_t& n_edges) {
+    G.occ = L2(&E.list_occ[u]);
+    G.mrow = L2(&E.list_mrow[u]);
     const uint64_t rs = L2(&E.list_rs[u]), re = L2(&E.list_re[u]);
-    const uint32_t only = E.unfused ? L2(&E.list_only[u]) : 0u;
-    const uint64_t q = (rs >> 2) + j;
-    const uint64_t e0 = q << 2;
-    const uint4 c4 = __ldg(reinterpret_cast<const uint4*>(E.col) + q);
-    uint4 t4 = __ldg(reinterpret_cast<const uint4*>(E.thr) + q);
-    if (e0 + 0 < rs || e0 + 0 >= re) t4.x = 0;
-    if (e0 + 1 < rs || e0 + 1 >= re) t4.y = 0;
-    if (e0 + 2 < rs || e0 + 2 >= re) t4.z = 0;
-    if (e0 + 3 < rs || e0 + 3 >= re) t4.w = 0;
-    n_edges += (uint64_t)min(re, e0 + 4) - (uint64_t)max(rs, e0);
-    if ((t4.x | t4.y | t4.z | t4.w) == 0) return;
-    // A draw is needed only for edges with 0 < thr < 0xFFFFFFFF.
-    const bool need = (t4.x - 1u < 0xFFFFFFFEu) || (t4.y - 1u < 0xFFFFFFFEu) || (t4.z - 1u < 0xFFFFFFFEu) ||
-                      (t4.w - 1u < 0xFFFFFFFEu);
-    uint64_t words = occ;
+    G.only = E.unfused ? L2(&E.list_only[u]) : 0u;
+    G.q = (rs >> 2) + j;
+    G.c4 = __ldg(reinterpret_cast<const uint4*>(E.col) + G.q);
+    const uint4 t = __ldg(reinterpret_cast<const uint4*>(E.thr) + G.q);
+    const uint32_t first = j == 0 ? (uint32_t)(rs & 3) : 0u;
+    const uint32_t last = G.q == ((re - 1) >> 2) ? (uint32_t)((re - 1) & 3) : 3u;
+    uint32_t inrow = (0xFu << first) & (0xFu >> (3u - last));
+    n_edges += __popc(inrow);
+    inrow &= (t.x ? 1u : 0u) | (t.y ? 2u : 0u) | (t.z ? 4u : 0u) | (t.w ? 8u : 0u);
+    G.valid = inrow;
+    G.sure = inrow & ((t.x == 0xFFFFFFFFu ? 1u : 0u) | (t.y == 0xFFFFFFFFu ? 2u : 0u) |
+                      (t.z == 0xFFFFFFFFu ? 4u : 0u) | (t.w == 0xFFFFFFFFu ? 8u : 0u));
+    G.tm = make_uint4(t.x == 0xFFFFFFFFu ? t.x : t.x - 1u, t.y == 0xFFFFFFFFu ? t.y : t.y - 1u,
+                      t.z == 0xFFFFFFFFu ? t.z : t.z - 1u, t.w == 0xFFFFFFFFu ? t.w : t.w - 1u);
+    return inrow != 0;
+}
+
+__device__ __forceinline__ void grp_run(const Eng& E, const Smem& sm, const Grp& G, const PhiloxKeys& K,
+                                        uint64_t& n_calls) {
+    const bool need = (G.valid & ~G.sure) != 0;  // some edge needs a draw
+    const uint32_t qlo = (uint32_t)G.q, qhi = (uint32_t)(G.q >> 32);
+    const uint32_t f_lo = (uint32_t)E.first_id, f_hi = (uint32_t)(E.first_id >> 32);
+    uint64_t words = G.occ;
     while (words) {
         const uint32_t i = __ffsll((long long)words) - 1;
         words &= words - 1;
-        const uint64_t x = only ? (1ull << ((only - 1u) & 63u)) : L2(&E.stage[(uint64_t)mrow * E.WB + i]);
+        const uint64_t x = G.only ? (1ull << ((G.only - 1u) & 63u)) : L2(&E.stage[(uint64_t)G.mrow * E.WB + i]);
         uint64_t y0, y1, y2, y3;
         if (need) {
-            y0 = y1 = y2 = y3 = 0;
-            uint64_t xx = x;
-            while (xx) {
-                const uint32_t c = __ffsll((long long)xx) - 1;
-                xx &= xx - 1;
-                const uint4 r = edge_draws4(E.seed, E.first_id + sm.lane[(i << 6) + c], q);
-                ++n_calls;
-                const uint64_t bit = 1ull << c;
-                if (live(r.x, t4.x)) y0 |= bit;
-                if (live(r.y, t4.y)) y1 |= bit;
-                if (live(r.z, t4.z)) y2 |= bit;
-                if (live(r.w, t4.w)) y3 |= bit;
+            uint32_t z[2][4];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                uint32_t xx = (uint32_t)(x >> (32 * h));
+                const uint32_t* lj = &sm.lane[(i << 6) + 32 * h];
+                uint32_t z0 = 0, z1 = 0, z2 = 0, z3 = 0;
+                while (xx) {
+                    const uint32_t c = __ffs(xx) - 1;
+                    xx &= xx - 1;
+                    const uint32_t j = lj[c];
+                    const uint32_t slo = f_lo + j;
+                    const uint32_t shi = f_hi + (slo < j ? 1u : 0u);
+                    const uint4 r = philox4x32_10(make_uint4(slo, shi, qlo, qhi), K);
+                    ++n_calls;
+                    const uint32_t bit = 1u << c;
+                    z0 |= r.x <= G.tm.x ? bit : 0u;
+                    z1 |= r.y <= G.tm.y ? bit : 0u;
+                    z2 |= r.z <= G.tm.z ? bit : 0u;
+                    z3 |= r.w <= G.tm.w ? bit : 0u;
+                }
+                z[h][0] = z0; z[h][1] = z1; z[h][2] = z2; z[h][3] = z3;
             }
+            y0 = ((uint64_t)z[1][0] << 32) | z[0][0];
+            y1 = ((uint64_t)z[1][1] << 32) | z[0][1];
+            y2 = ((uint64_t)z[1][2] << 32) | z[0][2];
+            y3 = ((uint64_t)z[1][3] << 32) | z[0][3];
         } else {
-            y0 = t4.x ? x : 0;
-            y1 = t4.y ? x : 0;
-            y2 = t4.z ? x : 0;
-            y3 = t4.w ? x : 0;
+            y0 = y1 = y2 = y3 = x;
         }
-        if (y0) or_next(E, c4.x, i, y0);
-        if (y1) or_next(E, c4.y, i, y1);
-        if (y2) or_next(E, c4.z, i, y2);
-        if (y3) or_next(E, c4.w, i, y3);
+        if ((G.valid & 1u) && y0) or_next(E, G.c4.x, i, y0);
+        if ((G.valid & 2u) && y1) or_next(E, G.c4.y, i, y1);
+        if ((G.valid & 4u) && y2) or_next(E, G.c4.z, i, y2);
+        if ((G.valid & 8u) && y3) or_next(E, G.c4.w, i, y3);
     }
+}
+
+// The unit holding group g of chunk c: chunk_u0[c] names the unit holding
+// group 32c; the lanes find their own unit among the (at most 32) units of the
+// chunk by binary lifting over shuffled group offsets.  All lanes must call.
+__device__ __forceinline__ uint32_t chunk_unit(const Eng& E, uint32_t c, uint64_t nchunks, uint64_t U, uint64_t g,
+                                               uint64_t& j) {
+    const uint32_t lane = lane_id();
+    const uint32_t u0 = L2(&E.chunk_u0[c]);
+    const uint32_t ul = (c + 1 < nchunks) ? L2(&E.chunk_u0[c + 1]) : (uint32_t)(U - 1);
+    const uint32_t nu = min(ul - u0 + 1u, 32u);
+    const uint64_t gb = lane < nu ? L2(&E.list_g[u0 + lane]) : ~0ull;
+    uint32_t k = 0;
+#pragma unroll
+    for (uint32_t step = 16; step > 0; step >>= 1) {
+        const uint64_t gs = __shfl_sync(0xffffffffu, gb, (k + step) & 31u);
+        if (k + step < nu && gs <= g) k += step;
+    }
+    j = g - __shfl_sync(0xffffffffu, gb, k);
+    return u0 + k;
 }
 
 // Edge-balanced: the frontier's 4-edge groups form one index space; a warp
 // takes kChunksPerGrab chunks of 32 consecutive groups per atomic, one group
-// per lane.  chunk_u0[c] names the unit holding group 32c; the lanes find
-// their own unit among the (at most 32) units of the chunk by binary lifting
-// over shuffled group offsets.
+// per lane, and works on two chunks at a time.
 __device__ void dev_expand(const Eng& E, Smem& sm) {
     Ctl* ctl = E.ctl;
     const uint64_t G = L2(&ctl->list_groups);
@@ -259,6 +310,7 @@ __device__ void dev_expand(const Eng& E, Smem& sm) {
     for (uint32_t l = threadIdx.x; l < 64u * E.WB; l += blockDim.x) sm.lane[l] = L2(&ctl->lane_j[l]);
     __syncthreads();
     const uint32_t lane = lane_id();
+    const PhiloxKeys K = philox_keys(E.seed);
     uint64_t n_edges = 0, n_calls = 0;
     for (;;) {
         uint32_t c0 = 0;
@@ -266,20 +318,19 @@ __device__ void dev_expand(const Eng& E, Smem& sm) {
         c0 = __shfl_sync(0xffffffffu, c0, 0);
         if (c0 >= nchunks) break;
         const uint32_t c1 = (uint32_t)min((uint64_t)c0 + kChunksPerGrab, nchunks);
-        for (uint32_t c = c0; c < c1; ++c) {
-            const uint64_t g = (uint64_t)c * kChunk + lane;
-            const uint32_t u0 = L2(&E.chunk_u0[c]);
-            const uint32_t ul = (c + 1 < nchunks) ? L2(&E.chunk_u0[c + 1]) : (uint32_t)(U - 1);
-            const uint32_t nu = min(ul - u0 + 1u, 32u);
-            const uint64_t gb = lane < nu ? L2(&E.list_g[u0 + lane]) : ~0ull;
-            uint32_t k = 0;
-#pragma unroll
-            for (uint32_t step = 16; step > 0; step >>= 1) {
-                const uint64_t gs = __shfl_sync(0xffffffffu, gb, (k + step) & 31u);
-                if (k + step < nu && gs <= g) k += step;
-            }
-            const uint64_t gk = __shfl_sync(0xffffffffu, gb, k);
-            if (g < G) expand_group(E, sm, u0 + k, g - gk, n_edges, n_calls);
+        for (uint32_t c = c0; c < c1; c += FBPT_EXPAND_ILP) {
+            const bool two = FBPT_EXPAND_ILP > 1 && c + 1 < c1;
+            const uint64_t ga = (uint64_t)c * kChunk + lane;
+            const uint64_t gbb = ga + kChunk;
+            uint64_t ja = 0, jb = 0;
+            const uint32_t ua = chunk_unit(E, c, nchunks, U, ga, ja);
+            uint32_t ub = 0;
+            if (two) ub = chunk_unit(E, c + 1, nchunks, U, gbb, jb);
+            Grp A, B;
+            const bool la = ga < G && grp_load(E, ua, ja, A, n_edges);
+            const bool lb = two && gbb < G && grp_load(E, ub, jb, B, n_edges);
+            if (la) grp_run(E, sm, A, K, n_calls);
+            if (lb) grp_run(E, sm, B, K, n_calls);
         }
     }
     n_edges = warp_sum(n_edges);
@@ -652,7 +703,7 @@ __global__ void __launch_bounds__(kThreads) k_sweep(const Eng E) {
     dev_sweep(E, sm);
 }
 __global__ void __launch_bounds__(kThreads) k_init(const Eng E) { dev_init(E); }
-__global__ void __launch_bounds__(kThreads) k_expand(const Eng E) {
+__global__ void __launch_bounds__(kThreads, FBPT_EXPAND_MINB) k_expand(const Eng E) {
     __shared__ Smem sm;
     dev_expand(E, sm);
 }
