@@ -201,6 +201,22 @@ int fbpt_rrsets_copy_to_host(const fbpt_rrsets* rr, uint64_t* offsets, uint32_t*
  * newly covered.  k > rr->n gives FBPT_EINVAL. */
 int fbpt_select_seeds(const fbpt_rrsets* rr, uint32_t k, uint32_t* seeds_host, uint64_t* gains_host);
 
+/* The same picks and gains as fbpt_select_seeds, for callers that cannot
+ * allocate device memory when they select seeds: for example a serving process
+ * that gives all free device memory to its own pool at start-up, or a thread on
+ * a latency-critical path that must stay clear of the allocator.  The paper has
+ * no counterpart; this is a property of the library, not of the method.
+ * It allocates nothing: its working memory is one fixed 64 MiB array in the
+ * library's device image, which every GPU that loads libfbpt holds until the
+ * process exits.  It needs 4*n + n + S + 20*k bytes (each part rounded up to
+ * 256) and returns FBPT_EINVAL, naming the limit, beyond 64 MiB.  The first
+ * call on a device looks up the array's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture.  All calls share the array
+ * and each starts by clearing it: calls whose work overlaps on the GPU (two
+ * host threads, or two streams) race and give wrong seeds, so serialize them.
+ * Work runs on rr->stream; the call returns after it finishes. */
+int fbpt_select_seeds_noalloc(const fbpt_rrsets* rr, uint32_t k, uint32_t* seeds_host, uint64_t* gains_host);
+
 /* ---- Building blocks exposed for verification ------------------------------------
  * Device results of the bit-level contract for given inputs (host arrays in
  * and out, count entries each): edge draws out[e & 3] for pairs (s[i], e[i]),

@@ -85,6 +85,7 @@ _SIGS = {
     "fbpt_rrsets_copy_to_host": (ctypes.c_int, [ctypes.POINTER(RRSetsC), ctypes.c_void_p, ctypes.c_void_p,
                                                 ctypes.c_void_p, ctypes.c_void_p]),
     "fbpt_select_seeds": (ctypes.c_int, [ctypes.POINTER(RRSetsC), ctypes.c_uint32, U32P, U64P]),
+    "fbpt_select_seeds_noalloc": (ctypes.c_int, [ctypes.POINTER(RRSetsC), ctypes.c_uint32, U32P, U64P]),
     "fbpt_edge_draws": (ctypes.c_int, [ctypes.c_uint64, U64P, U64P, ctypes.c_uint64, U32P]),
     "fbpt_start_vertices": (ctypes.c_int, [ctypes.c_uint64, U64P, ctypes.c_uint64, ctypes.c_uint32, U32P]),
     "fbpt_abi_sizes": (ctypes.c_int, [U64P, ctypes.c_int]),
@@ -273,6 +274,16 @@ def select_seeds(rr: RRSets, k: int):
     seeds = np.zeros(max(k, 1), np.uint32)
     gains = np.zeros(max(k, 1), np.uint64)
     _check(lib().fbpt_select_seeds(ctypes.byref(rr.c), k, _ptr_u32(seeds), _ptr_u64(gains)))
+    return seeds[:k], gains[:k]
+
+
+def select_seeds_noalloc(rr: RRSets, k: int):
+    """Greedy max-k-cover like select_seeds, but with the library's fixed
+    device array as working memory (fbpt_select_seeds_noalloc): no device
+    allocation, for callers that cannot allocate.  Calls must not overlap."""
+    seeds = np.zeros(max(k, 1), np.uint32)
+    gains = np.zeros(max(k, 1), np.uint64)
+    _check(lib().fbpt_select_seeds_noalloc(ctypes.byref(rr.c), k, _ptr_u32(seeds), _ptr_u64(gains)))
     return seeds[:k], gains[:k]
 
 

@@ -6,6 +6,8 @@
 // (vertex -> rows containing it) turns each pick into a walk over the newly
 // covered rows, decrementing the gain of every vertex in them.
 #include <algorithm>
+#include <mutex>
+#include <string>
 
 #include "internal.cuh"
 
@@ -141,4 +143,126 @@ extern "C" int fbpt_select_seeds(const fbpt_rrsets* rr, uint32_t k, uint32_t* se
     if (cudaStreamSynchronize(st) != cudaSuccess && rc == FBPT_OK)
         rc = fail(FBPT_ECUDA, std::string("fbpt_select_seeds: ") + cudaGetErrorString(cudaGetLastError()));
     return rc;
+}
+
+// ---- seed selection that allocates nothing ------------------------------------------------
+//
+// Some callers cannot allocate device memory at the point where they pick
+// seeds: a serving process that hands all free device memory to its own pool
+// at start-up (a cudaMalloc would fail or fragment that pool), or a host
+// thread on a latency-critical path that must not take the allocator's locks.
+// fbpt_select_seeds_noalloc gives them the same greedy picks as
+// fbpt_select_seeds with its working memory in the file-scope array below:
+// every GPU that loads libfbpt holds these 64 MiB until the process exits.
+// Instead of an inverted index it finds, each round, the uncovered rows that
+// contain the pick by a binary search in every row (rows are ascending).
+
+namespace fbpt {
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = 64ull << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_base[kMaxDevices] = {};
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Each thread takes uncovered rows; a row containing the pick is covered and
+// the gain of each of its vertices drops by one.
+__global__ void k_cover_rows(const unsigned long long* best, uint32_t r, uint32_t n, const uint64_t* offsets,
+                             const uint32_t* verts, uint64_t S, uint8_t* covered, uint32_t* gain, uint8_t* selected,
+                             uint32_t* seeds, uint64_t* gains) {
+    const unsigned long long key = best[r];
+    const uint32_t u = (uint32_t)(0xFFFFFFFFull - (key & 0xFFFFFFFFull));
+    if (key == 0 || u >= n) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        selected[u] = 1;
+        seeds[r] = u;
+        gains[r] = key >> 32;
+    }
+    for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < S; j += (uint64_t)gridDim.x * blockDim.x) {
+        if (covered[j]) continue;
+        uint64_t lo = offsets[j], hi = offsets[j + 1];
+        const uint64_t a = lo, b = hi;
+        while (lo < hi) {  // first position with verts[p] >= u
+            const uint64_t mid = (lo + hi) >> 1;
+            if (verts[mid] < u) lo = mid + 1; else hi = mid;
+        }
+        if (lo == b || verts[lo] != u) continue;
+        covered[j] = 1;
+        for (uint64_t p = a; p < b; ++p) atomicSub(&gain[verts[p]], 1u);
+    }
+}
+
+// Device address of the scratch array on the current device, looked up once
+// per device.
+int noalloc_base(void** out) {
+    int dev = 0;
+    FBPT_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return fail(FBPT_EUNSUPPORTED, "fbpt_select_seeds_noalloc: device index");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_base[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(FBPT_ECUDA, std::string("fbpt_select_seeds_noalloc: cudaGetSymbolAddress: ") +
+                                        cudaGetErrorString(e));
+        g_noalloc_base[dev] = p;
+    }
+    *out = g_noalloc_base[dev];
+    return FBPT_OK;
+}
+
+}  // namespace
+}  // namespace fbpt
+
+extern "C" int fbpt_select_seeds_noalloc(const fbpt_rrsets* rr, uint32_t k, uint32_t* seeds_host,
+                                         uint64_t* gains_host) {
+    if (!rr || !rr->offsets || !rr->vcount) return fail(FBPT_EINVAL, "fbpt_select_seeds_noalloc: null rrsets");
+    if (k > rr->n) return fail(FBPT_EINVAL, "fbpt_select_seeds_noalloc: k > n");
+    if (k == 0) return FBPT_OK;
+    if (!seeds_host) return fail(FBPT_EINVAL, "fbpt_select_seeds_noalloc: null seeds");
+    const uint32_t n = rr->n;
+    const uint64_t S = rr->S;
+    const size_t o_gain = 0;
+    const size_t o_sel = o_gain + align256(sizeof(uint32_t) * (size_t)n);
+    const size_t o_cov = o_sel + align256((size_t)n);
+    const size_t o_best = o_cov + align256((size_t)S);
+    const size_t o_seeds = o_best + align256(sizeof(unsigned long long) * k);
+    const size_t o_gains = o_seeds + align256(sizeof(uint32_t) * k);
+    const size_t need = o_gains + align256(sizeof(uint64_t) * k);
+    if (need > kNoAllocScratchBytes)
+        return fail(FBPT_EINVAL, "fbpt_select_seeds_noalloc: needs " + std::to_string(need) +
+                                     " bytes of scratch (5 bytes per vertex + 1 per RR set + 20 per seed), more "
+                                     "than its fixed " + std::to_string(kNoAllocScratchBytes) + " bytes");
+    void* basev = nullptr;
+    FBPT_TRY(noalloc_base(&basev));
+    unsigned char* base = static_cast<unsigned char*>(basev);
+    uint32_t* gain = reinterpret_cast<uint32_t*>(base + o_gain);
+    uint8_t* selected = base + o_sel;
+    uint8_t* covered = base + o_cov;
+    unsigned long long* best = reinterpret_cast<unsigned long long*>(base + o_best);
+    uint32_t* seeds = reinterpret_cast<uint32_t*>(base + o_seeds);
+    uint64_t* gains = reinterpret_cast<uint64_t*>(base + o_gains);
+    cudaStream_t st = (cudaStream_t)rr->stream;
+    // the array keeps the previous call's contents: start from zero
+    FBPT_CUDA_TRY(cudaMemsetAsync(selected, 0, n, st));
+    FBPT_CUDA_TRY(cudaMemsetAsync(covered, 0, S, st));
+    FBPT_CUDA_TRY(cudaMemsetAsync(best, 0, sizeof(unsigned long long) * k, st));
+    FBPT_CUDA_TRY(cudaMemcpyAsync(gain, rr->vcount, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, st));
+    const int sms = device_sm_count();
+    const int ablocks = (int)std::min<uint64_t>((n + 255) / 256, (uint64_t)sms * 8);
+    const int cblocks = (int)std::min<uint64_t>((S + 255) / 256, (uint64_t)sms * 8);
+    for (uint32_t r = 0; r < k; ++r) {
+        k_argmax<<<ablocks, 256, 0, st>>>(gain, selected, n, best + r);
+        k_cover_rows<<<cblocks, 256, 0, st>>>(best, r, n, rr->offsets, rr->verts, S, covered, gain, selected, seeds,
+                                              gains);
+    }
+    FBPT_CUDA_TRY(cudaGetLastError());
+    FBPT_CUDA_TRY(cudaMemcpyAsync(seeds_host, seeds, sizeof(uint32_t) * k, cudaMemcpyDeviceToHost, st));
+    if (gains_host) FBPT_CUDA_TRY(cudaMemcpyAsync(gains_host, gains, sizeof(uint64_t) * k, cudaMemcpyDeviceToHost, st));
+    FBPT_CUDA_TRY(cudaStreamSynchronize(st));
+    return FBPT_OK;
 }
