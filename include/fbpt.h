@@ -73,7 +73,8 @@ enum fbpt_schedule {
     FBPT_SCHED_PUSH = 0,      /* always push over in-edges of frontier vertices */
     FBPT_SCHED_PULL = 1,      /* always pull over out-edges of unvisited vertices */
     FBPT_SCHED_HEURISTIC = 2, /* degree-ratio rule picks push or pull per level */
-    FBPT_SCHED_LEARNED = 3    /* policy network picks, heuristic as fallback */
+    FBPT_SCHED_LEARNED = 3,   /* policy network picks, heuristic as fallback */
+    FBPT_SCHED_FILTERED = 4   /* always push, skipping draws for colours the source already has */
 };
 
 /* How the level loop is driven. */
@@ -104,8 +105,8 @@ typedef struct fbpt_trace_row {
     uint64_t finished_lanes; /* lanes whose sample ended at this level */
     uint64_t started_lanes;  /* lanes given a new sample at this level */
     uint64_t expand_ns, commit_ns, sweep_ns;  /* device time of each phase (%globaltimer) */
-    uint32_t direction;      /* 0 push, 1 pull */
-    uint32_t reserved;
+    uint32_t direction;      /* how this level expanded: 0 push, 1 filtered push, 2 pull */
+    uint32_t frontier_lanes; /* lanes with colours in this level's frontier */
 } fbpt_trace_row;
 
 typedef struct fbpt_graph fbpt_graph;
@@ -216,6 +217,22 @@ int fbpt_select_seeds(const fbpt_rrsets* rr, uint32_t k, uint32_t* seeds_host, u
  * host threads, or two streams) race and give wrong seeds, so serialize them.
  * Work runs on rr->stream; the call returns after it finishes. */
 int fbpt_select_seeds_noalloc(const fbpt_rrsets* rr, uint32_t k, uint32_t* seeds_host, uint64_t* gains_host);
+
+/* ---- Schedule policy --------------------------------------------------------------
+ * A 6 -> 32 -> 32 -> 8 ReLU network (FP32) that picks, per level, how the
+ * level expands (Section 9 (a): direction switching among push, push that
+ * skips colours the source already has, and pull).  Its outputs 0..2 are the
+ * predicted log2 device time of the level under each; the scheduler takes the
+ * smallest.  It changes the schedule only, never a bit of the output.
+ * Parameters (fbpt_policy_param_count() floats): input mean[6], input
+ * scale[6] (> 0), W1[32][6], b1[32], W2[32][32], b2[32], W3[8][32], b3[8];
+ * features as in fbpt_trace_row: log2(1+units), log2(1+groups),
+ * log2(1+colours), log2(1+frontier_lanes), log2(1+4*groups) - log2(1+m),
+ * log2(1+colours/units). */
+int fbpt_policy_param_count(void);
+int fbpt_policy_create(const float* params, uint64_t count, fbpt_policy** out);
+int fbpt_policy_destroy(fbpt_policy* p);
+int fbpt_policy_get(const fbpt_policy* p, float* params, uint64_t count);
 
 /* ---- Building blocks exposed for verification ------------------------------------
  * Device results of the bit-level contract for given inputs (host arrays in

@@ -23,7 +23,7 @@ LIB_PATH = os.path.join(_HERE, "libfbpt.so")
 HEADER = os.path.join(os.path.dirname(_HERE), "include", "fbpt.h")
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED, EDEVICE = 0, -1, -2, -3, -4, -5, -6
-SCHED = {"push": 0, "pull": 1, "heuristic": 2, "learned": 3}
+SCHED = {"push": 0, "pull": 1, "heuristic": 2, "learned": 3, "filtered": 4}
 LAUNCH = {"host": 0, "graph": 1, "persistent": 2}
 
 U64P = ctypes.POINTER(ctypes.c_uint64)
@@ -58,7 +58,7 @@ class Stats(ctypes.Structure):
 TRACE_DTYPE = np.dtype([(k, np.uint64) for k in
                         ("level", "units", "groups", "colours", "pending", "active_lanes", "finished_lanes",
                          "started_lanes", "expand_ns", "commit_ns", "sweep_ns")] +
-                       [("direction", np.uint32), ("reserved", np.uint32)])
+                       [("direction", np.uint32), ("frontier_lanes", np.uint32)])
 
 
 class FbptError(RuntimeError):
@@ -89,6 +89,11 @@ _SIGS = {
     "fbpt_edge_draws": (ctypes.c_int, [ctypes.c_uint64, U64P, U64P, ctypes.c_uint64, U32P]),
     "fbpt_start_vertices": (ctypes.c_int, [ctypes.c_uint64, U64P, ctypes.c_uint64, ctypes.c_uint32, U32P]),
     "fbpt_abi_sizes": (ctypes.c_int, [U64P, ctypes.c_int]),
+    "fbpt_policy_param_count": (ctypes.c_int, []),
+    "fbpt_policy_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_float), ctypes.c_uint64,
+                                          ctypes.POINTER(ctypes.c_void_p)]),
+    "fbpt_policy_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "fbpt_policy_get": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float), ctypes.c_uint64]),
     "fbpt_last_error": (ctypes.c_char_p, []),
     "fbpt_version": (ctypes.c_int, []),
 }
@@ -229,7 +234,7 @@ def make_opts(words=0, slots=0, schedule="push", launch="persistent", unfused=Fa
     o.schedule = SCHED[schedule] if isinstance(schedule, str) else int(schedule)
     o.launch = LAUNCH[launch] if isinstance(launch, str) else int(launch)
     o.unfused = int(bool(unfused))
-    o.policy = policy
+    o.policy = policy._h.value if isinstance(policy, Policy) else policy
     o.stream = stream
     return o
 
@@ -285,6 +290,32 @@ def select_seeds_noalloc(rr: RRSets, k: int):
     gains = np.zeros(max(k, 1), np.uint64)
     _check(lib().fbpt_select_seeds_noalloc(ctypes.byref(rr.c), k, _ptr_u32(seeds), _ptr_u64(gains)))
     return seeds[:k], gains[:k]
+
+
+class Policy:
+    """Schedule-policy network parameters on the device (fbpt_policy)."""
+
+    def __init__(self, params):
+        params = np.ascontiguousarray(params, np.float32)
+        self._h = ctypes.c_void_p()
+        _check(lib().fbpt_policy_create(params.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), params.size,
+                                        ctypes.byref(self._h)))
+
+    def params(self):
+        out = np.zeros(lib().fbpt_policy_param_count(), np.float32)
+        _check(lib().fbpt_policy_get(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), out.size))
+        return out
+
+    def close(self):
+        if self._h:
+            lib().fbpt_policy_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def edge_draws(seed: int, s, e):

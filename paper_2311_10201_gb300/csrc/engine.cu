@@ -72,7 +72,8 @@ struct Smem {
     uint64_t fin[kMaxWords];        // sweep: finished lanes (spill-log sweep)
     uint32_t cnt[kMaxWords + 1];    // schedule: per-word counts, then their prefix
     uint32_t tsum[kThreads + 1];    // schedule: per-thread sums of the block scan
-    uint32_t last, abort, nstill;
+    float feat[8], h1[kPolicyHidden], h2[kPolicyHidden], out[kPolicyOut];
+    uint32_t last, abort, nstill, dir;
 };
 
 __device__ __forceinline__ void phase_begin(Ctl* ctl, int p) {
@@ -228,7 +229,7 @@ __device__ __forceinline__ bool grp_load(const Eng& E, uint32_t u, uint64_t j, G
 }
 
 __device__ __forceinline__ void grp_run(const Eng& E, const Smem& sm, const Grp& G, const PhiloxKeys& K,
-                                        uint64_t& n_calls) {
+                                        bool filtered, uint64_t& n_calls) {
     const bool need = (G.valid & ~G.sure) != 0;  // some edge needs a draw
     const uint32_t qlo = (uint32_t)G.q, qhi = (uint32_t)(G.q >> 32);
     const uint32_t f_lo = (uint32_t)E.first_id, f_hi = (uint32_t)(E.first_id >> 32);
@@ -236,7 +237,17 @@ __device__ __forceinline__ void grp_run(const Eng& E, const Smem& sm, const Grp&
     while (words) {
         const uint32_t i = __ffsll((long long)words) - 1;
         words &= words - 1;
-        const uint64_t x = G.only ? (1ull << ((G.only - 1u) & 63u)) : L2(&E.stage[(uint64_t)G.mrow * E.WB + i]);
+        uint64_t x = G.only ? (1ull << ((G.only - 1u) & 63u)) : L2(&E.stage[(uint64_t)G.mrow * E.WB + i]);
+        // filtered push: a colour the source has already seen needs no draw
+        uint64_t v0 = ~0ull, v1 = ~0ull, v2 = ~0ull, v3 = ~0ull;
+        if (filtered) {
+            if (G.valid & 1u) v0 = L2(&E.visited[(uint64_t)G.c4.x * E.WB + i]);
+            if (G.valid & 2u) v1 = L2(&E.visited[(uint64_t)G.c4.y * E.WB + i]);
+            if (G.valid & 4u) v2 = L2(&E.visited[(uint64_t)G.c4.z * E.WB + i]);
+            if (G.valid & 8u) v3 = L2(&E.visited[(uint64_t)G.c4.w * E.WB + i]);
+            x &= ~(v0 & v1 & v2 & v3);
+            if (!x) continue;
+        }
         uint64_t y0, y1, y2, y3;
         if (need) {
             uint32_t z[2][4];
@@ -268,6 +279,12 @@ __device__ __forceinline__ void grp_run(const Eng& E, const Smem& sm, const Grp&
         } else {
             y0 = y1 = y2 = y3 = x;
         }
+        if (filtered) {
+            y0 &= ~v0;
+            y1 &= ~v1;
+            y2 &= ~v2;
+            y3 &= ~v3;
+        }
         if ((G.valid & 1u) && y0) or_next(E, G.c4.x, i, y0);
         if ((G.valid & 2u) && y1) or_next(E, G.c4.y, i, y1);
         if ((G.valid & 4u) && y2) or_next(E, G.c4.z, i, y2);
@@ -295,6 +312,83 @@ __device__ __forceinline__ uint32_t chunk_unit(const Eng& E, uint32_t c, uint64_
     return u0 + k;
 }
 
+// Pull (Section 9 (a), direction switching): every vertex w that some
+// frontier colour has not reached yet scans its out-edges (w -> v, edge e).  A
+// colour of the frontier row of v that w lacks is live by the same draw as in
+// push (word e & 3 of Philox(sample, e >> 2)), so the closure is unchanged.  A
+// warp owns w and stops once every missing colour has been found; no draw is
+// spent on a colour w already has.  Needs WB <= kPullMaxWords.
+__device__ void dev_pull(const Eng& E, const Smem& sm, const PhiloxKeys& K, uint64_t& n_edges, uint64_t& n_calls) {
+    Ctl* ctl = E.ctl;
+    const uint32_t WB = E.WB;
+    const uint32_t tick = (uint32_t)L2(&ctl->tick);
+    uint64_t still[kPullMaxWords];
+#pragma unroll
+    for (uint32_t i = 0; i < kPullMaxWords; ++i) still[i] = i < WB ? L2(&ctl->still_w[i]) : 0ull;
+    const uint32_t lane = lane_id();
+    const uint64_t wid = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarp = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const uint32_t f_lo = (uint32_t)E.first_id, f_hi = (uint32_t)(E.first_id >> 32);
+    for (uint64_t w = wid; w < E.n; w += nwarp) {
+        uint64_t cand[kPullMaxWords];
+        bool any = false;
+#pragma unroll
+        for (uint32_t i = 0; i < kPullMaxWords; ++i) {
+            cand[i] = still[i] ? (still[i] & ~L2(&E.visited[w * WB + i])) : 0ull;
+            any |= cand[i] != 0;
+        }
+        if (!any) continue;
+        const uint64_t a = __ldg(&E.orow[w]), b = __ldg(&E.orow[w + 1]);
+        uint64_t acc[kPullMaxWords];
+#pragma unroll
+        for (uint32_t i = 0; i < kPullMaxWords; ++i) acc[i] = 0;
+        for (uint64_t base = a; base < b; base += 32) {
+            const uint64_t p = base + lane;
+            if (p < b) {
+                const uint32_t v = __ldg(&E.odst[p]);
+                if (L2(&E.fstamp[v]) == tick) {
+                    const uint32_t e = __ldg(&E.oeid[p]);
+                    const uint32_t t = __ldg(&E.thr[e]);
+                    ++n_edges;
+#pragma unroll
+                    for (uint32_t i = 0; i < kPullMaxWords; ++i) {
+                        if (!cand[i] || !t) continue;
+                        uint64_t f = L2(&E.frontd[(uint64_t)v * WB + i]) & cand[i] & ~acc[i];
+                        if (t == 0xFFFFFFFFu) {
+                            acc[i] |= f;
+                            continue;
+                        }
+                        while (f) {
+                            const uint32_t c = __ffsll((long long)f) - 1;
+                            f &= f - 1;
+                            const uint32_t j = sm.lane[(i << 6) + c];
+                            const uint32_t slo = f_lo + j;
+                            const uint32_t shi = f_hi + (slo < j ? 1u : 0u);
+                            const uint4 r = philox4x32_10(make_uint4(slo, shi, e >> 2, 0u), K);
+                            ++n_calls;
+                            const uint32_t k = e & 3u;
+                            const uint32_t draw = k == 0 ? r.x : k == 1 ? r.y : k == 2 ? r.z : r.w;
+                            if (draw < t) acc[i] |= 1ull << c;
+                        }
+                    }
+                }
+            }
+            bool left = false;
+#pragma unroll
+            for (uint32_t i = 0; i < kPullMaxWords; ++i) {
+                acc[i] = warp_or64(acc[i]);
+                left |= (cand[i] & ~acc[i]) != 0;
+            }
+            if (!left) break;
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (uint32_t i = 0; i < kPullMaxWords; ++i)
+                if (acc[i]) or_next(E, (uint32_t)w, i, acc[i]);
+        }
+    }
+}
+
 // Edge-balanced: the frontier's 4-edge groups form one index space; a warp
 // takes kChunksPerGrab chunks of 32 consecutive groups per atomic, one group
 // per lane, and works on two chunks at a time.
@@ -312,7 +406,10 @@ __device__ void dev_expand(const Eng& E, Smem& sm) {
     const uint32_t lane = lane_id();
     const PhiloxKeys K = philox_keys(E.seed);
     uint64_t n_edges = 0, n_calls = 0;
-    for (;;) {
+    const uint32_t dir = L2(&ctl->dir);
+    const bool filtered = dir == kDirFiltered;
+    if (dir == kDirPull && E.frontd) dev_pull(E, sm, K, n_edges, n_calls);
+    else for (;;) {
         uint32_t c0 = 0;
         if (lane == 0) c0 = atomicAdd(&ctl->chunk_next, kChunksPerGrab);
         c0 = __shfl_sync(0xffffffffu, c0, 0);
@@ -329,8 +426,8 @@ __device__ void dev_expand(const Eng& E, Smem& sm) {
             Grp A, B;
             const bool la = ga < G && grp_load(E, ua, ja, A, n_edges);
             const bool lb = two && gbb < G && grp_load(E, ub, jb, B, n_edges);
-            if (la) grp_run(E, sm, A, K, n_calls);
-            if (lb) grp_run(E, sm, B, K, n_calls);
+            if (la) grp_run(E, sm, A, K, filtered, n_calls);
+            if (lb) grp_run(E, sm, B, K, filtered, n_calls);
         }
     }
     n_edges = warp_sum(n_edges);
@@ -454,6 +551,11 @@ __device__ void dev_commit(const Eng& E, Smem& sm) {
         __syncwarp();
         const uint64_t ng = occ ? row_groups(rs, re) : 0;
         const uint64_t units = ng ? (E.unfused ? bits : 1u) : 0u;
+        if (E.frontd && units) {  // frontier row by vertex, for a pull level
+            for (uint32_t i = 0; i < E.WB; ++i)
+                E.frontd[(uint64_t)w * E.WB + i] = ((occ >> i) & 1ull) ? L2(&E.stage[idx * E.WB + i]) : 0ull;
+            E.fstamp[w] = (uint32_t)L2(&ctl->tick) + 1u;
+        }
         mwords += units ? (E.unfused ? units : (uint64_t)__popcll(occ)) : 0;
         ncol += units ? bits : 0;
         const unsigned long long req = (unsigned long long)((units * ng) << kUnitBits) | units;
@@ -513,6 +615,67 @@ __device__ void dev_commit(const Eng& E, Smem& sm) {
         if (a) atomicOr(&ctl->act_w[i], a);
     }
     if (P) phase_end(ctl, 1);
+}
+
+// ---- level direction: degree-ratio heuristic and the policy network ----------------------
+
+// Features of the coming level (also what the trace rows let a trainer rebuild):
+// log2 of 1 + units, groups, colours and frontier lanes, the frontier's share of
+// the edges (log2 of 4 * groups / m) and log2 of colours per unit.
+__device__ __forceinline__ void level_features(float* f, double U, double G, double C, double L, double m) {
+    f[0] = (float)log2(1.0 + U);
+    f[1] = (float)log2(1.0 + G);
+    f[2] = (float)log2(1.0 + C);
+    f[3] = (float)log2(1.0 + L);
+    f[4] = (float)(log2(1.0 + 4.0 * G) - log2(1.0 + m));
+    f[5] = (float)log2(1.0 + C / (U > 1.0 ? U : 1.0));
+}
+
+// Push draws about G * (colours per unit) times; a pull level reads every
+// vertex's row and, at most, every edge.  Pull when the push would draw for more
+// colour-edges than twice the edge count; filter pushes whose units carry many
+// colours (their targets are likelier to have seen them already).
+__device__ __forceinline__ uint32_t heuristic_dir(double U, double G, double C, double m, bool pull_ok) {
+    const double cbar = C / (U > 1.0 ? U : 1.0);
+    if (pull_ok && G * cbar > 2.0 * m) return kDirPull;
+    if (cbar >= 8.0) return kDirFiltered;
+    return kDirPush;
+}
+
+// 6 -> 32 -> 32 -> 8 ReLU network; outputs 0..2 are the predicted log2 device
+// time of the level under push, filtered push and pull.  P holds the input
+// mean and scale (6 + 6), then W1 (32x6), b1, W2 (32x32), b2, W3 (8x32), b3.
+// All threads of the CTA call it.
+__device__ void policy_forward(const float* P, Smem& sm) {
+    const int t = threadIdx.x;
+    const float* mu = P;
+    const float* sd = P + kPolicyIn;
+    const float* W1 = P + 2 * kPolicyIn;
+    const float* b1 = W1 + kPolicyIn * kPolicyHidden;
+    const float* W2 = b1 + kPolicyHidden;
+    const float* b2 = W2 + kPolicyHidden * kPolicyHidden;
+    const float* W3 = b2 + kPolicyHidden;
+    const float* b3 = W3 + kPolicyHidden * kPolicyOut;
+    if (t < kPolicyIn) sm.feat[t] = (sm.feat[t] - mu[t]) / sd[t];
+    __syncthreads();
+    if (t < kPolicyHidden) {
+        float h = b1[t];
+        for (int k = 0; k < kPolicyIn; ++k) h += W1[t * kPolicyIn + k] * sm.feat[k];
+        sm.h1[t] = h > 0.f ? h : 0.f;
+    }
+    __syncthreads();
+    if (t < kPolicyHidden) {
+        float h = b2[t];
+        for (int k = 0; k < kPolicyHidden; ++k) h += W2[t * kPolicyHidden + k] * sm.h1[k];
+        sm.h2[t] = h > 0.f ? h : 0.f;
+    }
+    __syncthreads();
+    if (t < kPolicyOut) {
+        float o = b3[t];
+        for (int k = 0; k < kPolicyHidden; ++k) o += W3[t * kPolicyHidden + k] * sm.h2[k];
+        sm.out[t] = o;
+    }
+    __syncthreads();
 }
 
 // ---- schedule (one CTA, at least kMaxWords threads) ------------------------------------
@@ -632,9 +795,38 @@ __device__ void dev_schedule(const Eng& E, Smem& sm) {
         }
         ctl->init_w[i] = init;
         ctl->run_w[i] = still | init;
+        ctl->still_w[i] = still;
         ctl->act_w[i] = 0;
     }
     const bool any_run = __syncthreads_or((still | init) != 0);
+    // direction of the coming level
+    {
+        const unsigned long long np = L2(&ctl->new_packed);
+        const double U = (double)(np & kUnitMask), G = (double)(np >> kUnitBits);
+        const double C = (double)L2(&ctl->new_colours);
+        const uint32_t sched = L2(&ctl->sched);
+        const bool pull_ok = E.frontd != nullptr;
+        if (threadIdx.x == 0) {
+            level_features(sm.feat, U, G, C, (double)sm.nstill, (double)E.m);
+            uint32_t d = kDirPush;
+            if (sched == FBPT_SCHED_PULL && pull_ok) d = kDirPull;
+            else if (sched == FBPT_SCHED_FILTERED) d = kDirFiltered;
+            else if (sched == FBPT_SCHED_HEURISTIC || sched == FBPT_SCHED_LEARNED)
+                d = heuristic_dir(U, G, C, (double)E.m, pull_ok);
+            sm.dir = d;
+        }
+        __syncthreads();
+        if (sched == FBPT_SCHED_LEARNED && E.policy) {
+            policy_forward(E.policy, sm);
+            if (threadIdx.x == 0) {
+                uint32_t best = kDirPush;
+                if (sm.out[kDirFiltered] < sm.out[best]) best = kDirFiltered;
+                if (pull_ok && sm.out[kDirPull] < sm.out[best]) best = kDirPull;
+                sm.dir = best;
+            }
+            __syncthreads();
+        }
+    }
     if (threadIdx.x == 0) {
         // a lane whose segment overflowed has entries in the spill log: the next
         // sweep reads the log and writes the surviving entries to the other buffer
@@ -646,6 +838,7 @@ __device__ void dev_schedule(const Eng& E, Smem& sm) {
         ctl->spill_sweep = any_spill ? 1u : 0u;
         const uint64_t assigned = min((uint64_t)sm.cnt[E.WB], avail);
         const unsigned long long tick = L2(&ctl->tick);
+        const unsigned long long done_groups = L2(&ctl->list_groups);  // the level just expanded
         if (E.trace && tick < E.trace_cap) {
             fbpt_trace_row& row = E.trace[tick];
             row.level = tick;
@@ -661,8 +854,8 @@ __device__ void dev_schedule(const Eng& E, Smem& sm) {
                 const unsigned long long t0 = L2(&ctl->ph_t0[p]), t1 = L2(&ctl->ph_t1[p]);
                 *pt[p] = t1 > t0 ? t1 - t0 : 0;
             }
-            row.direction = 0;
-            row.reserved = 0;
+            row.direction = L2(&ctl->dir);
+            row.frontier_lanes = L2(&ctl->frontier_lanes);
         }
         ctl->list_colours = err ? 0 : L2(&ctl->new_colours);
         ctl->new_colours = 0;
@@ -672,7 +865,11 @@ __device__ void dev_schedule(const Eng& E, Smem& sm) {
         ctl->list_count = err ? 0 : (np & kUnitMask);
         ctl->list_groups = err ? 0 : (np >> kUnitBits);
         ctl->st_units += np & kUnitMask;
-        if ((np >> kUnitBits) != 0) ctl->st_push += 1;
+        if (done_groups != 0) {
+            if (L2(&ctl->dir) == kDirPull) ctl->st_pull += 1; else ctl->st_push += 1;
+        }
+        ctl->dir = sm.dir;
+        ctl->frontier_lanes = sm.nstill;
         for (int p = 0; p < 3; ++p) {
             const unsigned long long t0 = L2(&ctl->ph_t0[p]), t1 = L2(&ctl->ph_t1[p]);
             if (t1 > t0) ctl->st_phase_ns[p] += t1 - t0;
@@ -922,6 +1119,7 @@ void ws_free(Workspace* w) {
     cudaFree(w->visited); cudaFree(w->next); cudaFree(w->nocc); cudaFree(w->stage); cudaFree(w->pend_v);
     cudaFree(w->seg); cudaFree(w->spill); cudaFree(w->list_v); cudaFree(w->list_mrow); cudaFree(w->list_only); cudaFree(w->list_rs);
     cudaFree(w->list_re); cudaFree(w->list_g); cudaFree(w->list_occ); cudaFree(w->chunk_u0); cudaFree(w->ctl);
+    cudaFree(w->frontd); cudaFree(w->fstamp);
     if (w->ctl_host) cudaFreeHost(w->ctl_host);
     delete w;
 }
@@ -935,9 +1133,9 @@ int ws_zero(Workspace* w, cudaStream_t st) {
     return FBPT_OK;
 }
 
-int ws_get(fbpt_graph* g, uint32_t WB, bool unfused, cudaStream_t st, Workspace** out) {
+int ws_get(fbpt_graph* g, uint32_t WB, bool unfused, bool dense, cudaStream_t st, Workspace** out) {
     Workspace* w = g->ws;
-    if (w && w->WB == WB && w->unfused == unfused) {
+    if (w && w->WB == WB && w->unfused == unfused && (w->frontd != nullptr) == dense) {
         if (!w->clean) FBPT_TRY(ws_zero(w, st));
         *out = w;
         return FBPT_OK;
@@ -978,6 +1176,8 @@ int ws_get(fbpt_graph* g, uint32_t WB, bool unfused, cudaStream_t st, Workspace*
     if (rc == FBPT_OK) rc = dalloc(&w->list_occ, w->list_cap, b);
     if (rc == FBPT_OK) rc = dalloc(&w->chunk_u0, w->chunk_cap, b);
     if (rc == FBPT_OK) rc = dalloc(&w->ctl, 1, b);
+    if (rc == FBPT_OK && dense) rc = dalloc(&w->frontd, rows, b);
+    if (rc == FBPT_OK && dense) rc = dalloc(&w->fstamp, n, b);
     if (rc == FBPT_OK && cudaMallocHost((void**)&w->ctl_host, sizeof(Ctl)) != cudaSuccess)
         rc = fail(FBPT_ENOMEM, "cudaMallocHost(ctl) failed");
     if (rc == FBPT_OK) rc = ws_zero(w, st);
@@ -1021,8 +1221,15 @@ int sample_impl(fbpt_graph* g, uint64_t seed, uint64_t first_id, uint64_t S, con
     uint32_t WB = W * B;
     // never more lanes than samples (rounded up to whole words)
     WB = (uint32_t)std::min<uint64_t>(WB, (S + 63) / 64);
-    if (o.schedule != FBPT_SCHED_PUSH && o.schedule != FBPT_SCHED_HEURISTIC && o.schedule != FBPT_SCHED_LEARNED)
-        return fail(FBPT_EUNSUPPORTED, "fbpt_sample: schedule not available");
+    if (o.schedule > FBPT_SCHED_FILTERED) return fail(FBPT_EINVAL, "fbpt_sample: bad schedule");
+    // pull levels need dense frontier rows (WB <= 8 words), fused units and 32-bit edge ids
+    const bool pull_ok = WB <= kPullMaxWords && !o.unfused && g->m < (1ull << 32);
+    if (o.schedule == FBPT_SCHED_PULL && !pull_ok)
+        return fail(FBPT_EUNSUPPORTED, "fbpt_sample: pull needs words * slots <= 8, fused units and m < 2^32");
+    const bool dense = pull_ok && (o.schedule == FBPT_SCHED_PULL || o.schedule == FBPT_SCHED_HEURISTIC ||
+                                   o.schedule == FBPT_SCHED_LEARNED);
+    if (o.schedule == FBPT_SCHED_LEARNED && o.policy && !o.policy->d_params)
+        return fail(FBPT_EINVAL, "fbpt_sample: policy has no parameters");
     if (o.launch != FBPT_LAUNCH_HOST && o.launch != FBPT_LAUNCH_GRAPH && o.launch != FBPT_LAUNCH_PERSISTENT)
         return fail(FBPT_EINVAL, "fbpt_sample: bad launch mode");
     if (o.refill != FBPT_REFILL_LANE && o.refill != FBPT_REFILL_BATCH)
@@ -1037,8 +1244,9 @@ int sample_impl(fbpt_graph* g, uint64_t seed, uint64_t first_id, uint64_t S, con
     cudaEventCreate(&ev1);
     cudaEventRecord(ev0, st);
 
+    if (dense) FBPT_TRY(ensure_out_csr(g, st));
     Workspace* ws = nullptr;
-    FBPT_TRY(ws_get(g, WB, o.unfused != 0, st, &ws));
+    FBPT_TRY(ws_get(g, WB, o.unfused != 0, dense, st, &ws));
 
     std::memset(out, 0, sizeof(*out));
     out->S = S;
@@ -1061,12 +1269,15 @@ int sample_impl(fbpt_graph* g, uint64_t seed, uint64_t first_id, uint64_t S, con
         FBPT_CUDA_TRY(cudaMemsetAsync(out->vcount, 0, sizeof(uint32_t) * g->n, st));
         std::memset(H, 0, sizeof(Ctl));
         H->S = S;
+        H->sched = o.schedule;
+        H->dir = o.schedule == FBPT_SCHED_FILTERED ? kDirFiltered : kDirPush;
         H->refill = o.refill == FBPT_REFILL_BATCH ? kRefillBatch : kRefillLane;
         H->pair_cap = cap;
         for (int p = 0; p < 3; ++p) H->ph_t0[p] = ~0ull;
         const uint64_t waves = S / (64ull * WB) + 2;
         H->tick_limit = std::min<uint64_t>(waves * ((uint64_t)g->n + 2) + 16, 1ull << 40);
         FBPT_CUDA_TRY(cudaMemcpyAsync(ws->ctl, H, sizeof(Ctl), cudaMemcpyHostToDevice, st));
+        if (ws->fstamp) FBPT_CUDA_TRY(cudaMemsetAsync(ws->fstamp, 0xFF, sizeof(uint32_t) * g->n, st));
 
         Eng E = {};
         E.n = g->n; E.WB = WB;
@@ -1077,6 +1288,10 @@ int sample_impl(fbpt_graph* g, uint64_t seed, uint64_t first_id, uint64_t S, con
         E.list_v = ws->list_v; E.list_mrow = ws->list_mrow; E.list_only = ws->list_only;
         E.list_rs = ws->list_rs; E.list_re = ws->list_re; E.list_g = ws->list_g; E.list_occ = ws->list_occ;
         E.chunk_u0 = ws->chunk_u0;
+        E.orow = g->orow; E.odst = g->odst; E.oeid = g->oeid;
+        E.frontd = ws->frontd; E.fstamp = ws->fstamp;
+        E.policy = (o.schedule == FBPT_SCHED_LEARNED && o.policy) ? o.policy->d_params : nullptr;
+        E.m = g->m;
         E.pend_cap = ws->pend_cap; E.list_cap = ws->list_cap; E.chunk_cap = ws->chunk_cap;
         E.spill_cap = ws->spill_cap;
         E.unfused = o.unfused ? 1u : 0u;
@@ -1172,6 +1387,7 @@ int sample_impl(fbpt_graph* g, uint64_t seed, uint64_t first_id, uint64_t S, con
         stats->levels += H->tick;
         stats->batches += (S + 64ull * WB - 1) / (64ull * WB);
         stats->push_levels += H->st_push;
+        stats->pull_levels += H->st_pull;
         stats->units_expanded += H->st_units;
         stats->edge_accesses += H->st_edges;
         stats->philox_calls += H->st_calls;

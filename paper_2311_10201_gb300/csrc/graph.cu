@@ -21,7 +21,53 @@ __global__ void k_validate(const uint64_t* row_ptr, const uint32_t* col, uint32_
         if (col[e] >= n) atomicOr(err, 8u);
 }
 
+__global__ void k_outdeg(const uint32_t* col, uint64_t m, uint32_t* deg) {
+    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (uint64_t)gridDim.x * blockDim.x)
+        atomicAdd(&deg[col[e]], 1u);
+}
+
+// One warp per in-row v: each in-edge e = (w -> v) goes to out-row w as (v, e).
+__global__ void k_outfill(const uint64_t* row_ptr, const uint32_t* col, uint32_t n, const uint64_t* orow,
+                          uint32_t* cursor, uint32_t* odst, uint32_t* oeid) {
+    const uint32_t lane = lane_id();
+    const uint64_t wid = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarp = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t v = wid; v < n; v += nwarp)
+        for (uint64_t e = row_ptr[v] + lane; e < row_ptr[v + 1]; e += 32) {
+            const uint32_t w = col[e];
+            const uint64_t p = orow[w] + atomicAdd(&cursor[w], 1u);
+            odst[p] = (uint32_t)v;
+            oeid[p] = (uint32_t)e;
+        }
+}
+
 }  // namespace
+
+int ensure_out_csr(fbpt_graph* g, cudaStream_t st) {
+    if (g->orow) return FBPT_OK;
+    if (g->m >= (1ull << 32)) return fail(FBPT_EUNSUPPORTED, "pull levels need fewer than 2^32 edges");
+    uint32_t* cnt = nullptr;
+    FBPT_CUDA_TRY(cudaMalloc(&g->orow, sizeof(uint64_t) * ((uint64_t)g->n + 1)));
+    FBPT_CUDA_TRY(cudaMalloc(&g->odst, sizeof(uint32_t) * std::max<uint64_t>(g->m, 1)));
+    FBPT_CUDA_TRY(cudaMalloc(&g->oeid, sizeof(uint32_t) * std::max<uint64_t>(g->m, 1)));
+    FBPT_CUDA_TRY(cudaMallocAsync(&cnt, sizeof(uint32_t) * g->n, st));
+    FBPT_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * g->n, st));
+    const int sms = device_sm_count();
+    k_outdeg<<<sms * 8, 256, 0, st>>>(g->col, g->m, cnt);
+    int rc = exclusive_scan_u32(cnt, g->orow, g->n, st);
+    if (rc == FBPT_OK) {
+        FBPT_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * g->n, st));
+        k_outfill<<<sms * 8, 256, 0, st>>>(g->row_ptr, g->col, g->n, g->orow, cnt, g->odst, g->oeid);
+        FBPT_CUDA_TRY(cudaGetLastError());
+    }
+    cudaFreeAsync(cnt, st);
+    if (rc != FBPT_OK) {
+        cudaFree(g->orow); cudaFree(g->odst); cudaFree(g->oeid);
+        g->orow = nullptr; g->odst = nullptr; g->oeid = nullptr;
+    }
+    return rc;
+}
+
 }  // namespace fbpt
 
 using namespace fbpt;
@@ -89,6 +135,9 @@ extern "C" int fbpt_graph_destroy(fbpt_graph* g) {
     if (g->stream) cudaStreamSynchronize(g->stream);
     cudaDeviceSynchronize();
     workspace_release(g);
+    cudaFree(g->orow);
+    cudaFree(g->odst);
+    cudaFree(g->oeid);
     cudaFree(g->row_ptr);
     cudaFree(g->col);
     cudaFree(g->thr);

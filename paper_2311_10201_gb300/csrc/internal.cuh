@@ -25,6 +25,17 @@ enum ErrorBits : uint32_t {
     kErrSpillOverflow = 32u,
 };
 
+// How a level expands its frontier.
+enum Direction : uint32_t {
+    kDirPush = 0,      // push over in-edges of frontier units; draws for every frontier colour
+    kDirFiltered = 1,  // push, skipping colours the source has already seen (gathers visited[w])
+    kDirPull = 2,      // pull over out-edges of vertices not yet visited by every frontier colour
+};
+constexpr uint32_t kPullMaxWords = 8;  // pull levels need WB <= 8 (dense frontier rows)
+constexpr int kPolicyIn = 6, kPolicyHidden = 32, kPolicyOut = 8;
+constexpr int kPolicyParams = kPolicyIn * kPolicyHidden + kPolicyHidden + kPolicyHidden * kPolicyHidden +
+                              kPolicyHidden + kPolicyHidden * kPolicyOut + kPolicyOut;
+
 enum RefillMode : uint32_t {
     kRefillLane = 0,   // a colour lane takes the next sample as soon as its traversal ends
     kRefillBatch = 1,  // lanes are refilled only when every lane of the row has finished
@@ -42,12 +53,16 @@ struct Ctl {
     unsigned int error;              // ErrorBits
     unsigned int refill;             // RefillMode
     unsigned int bar_count, bar_gen; // grid barrier of the persistent kernel
+    unsigned int dir;                // Direction of the coming level
+    unsigned int frontier_lanes;     // lanes with colours in the coming level's frontier
+    unsigned int sched;              // fbpt_schedule of the run
     unsigned long long tick, tick_limit;
     unsigned long long next_j, S;    // next sample index to hand out; samples in the run
     unsigned long long pair_cursor, pair_cap;
     unsigned long long run_w[kMaxWords];   // lanes holding a sample
     unsigned long long act_w[kMaxWords];   // lanes present in the new frontier
     unsigned long long init_w[kMaxWords];  // lanes given a sample at the last schedule (init input)
+    unsigned long long still_w[kMaxWords]; // lanes with colours in the current frontier
     unsigned int lane_j[kMaxLanes];        // sample index held by each lane
     unsigned int lane_cnt[kMaxLanes];      // RR entries of the lane's current sample so far
     unsigned int retired_j[kMaxLanes];     // sample index a finished lane held
@@ -88,6 +103,8 @@ struct Workspace {
     uint64_t* list_g = nullptr;
     uint64_t* list_occ = nullptr;
     uint32_t* chunk_u0 = nullptr; // chunk_cap
+    uint64_t* frontd = nullptr;   // n * WB when pull levels are allowed: frontier rows by vertex
+    uint32_t* fstamp = nullptr;   // n: level whose frontier frontd[v] holds
     uint64_t pend_cap = 0, list_cap = 0, chunk_cap = 0, spill_cap = 0;
     Ctl* ctl = nullptr;
     Ctl* ctl_host = nullptr;      // pinned mirror
@@ -117,6 +134,13 @@ struct Eng {
     uint64_t* list_g;
     uint64_t* list_occ;
     uint32_t* chunk_u0;
+    const uint64_t* orow;         // out-edge CSR (pull)
+    const uint32_t* odst;
+    const uint32_t* oeid;
+    uint64_t* frontd;
+    uint32_t* fstamp;
+    const float* policy;          // kPolicyParams weights of the schedule network, or NULL
+    uint64_t m;
     uint64_t pend_cap, list_cap, chunk_cap, spill_cap;
     uint32_t unfused;
     uint32_t vbits;               // bits of a vertex id in a pair key
@@ -132,6 +156,13 @@ struct Eng {
 
 }  // namespace fbpt
 
+// The opaque handle behind fbpt_policy*: the schedule network's parameters
+// (input mean and scale, then the three layers), on the device and the host.
+struct fbpt_policy {
+    float* d_params = nullptr;
+    float h_params[2 * fbpt::kPolicyIn + fbpt::kPolicyParams] = {};
+};
+
 // The opaque handle behind fbpt_graph*.
 struct fbpt_graph {
     uint32_t n = 0;
@@ -141,12 +172,19 @@ struct fbpt_graph {
     uint32_t* thr = nullptr;
     cudaStream_t stream = nullptr;
     int device = 0;
+    // out-edge CSR for pull levels, built on first use: out-row w lists
+    // (v, e) for every in-edge e = (w -> v)
+    uint64_t* orow = nullptr;     // n + 1
+    uint32_t* odst = nullptr;     // m
+    uint32_t* oeid = nullptr;     // m (edge ids < 2^32)
     fbpt::Workspace* ws = nullptr;
     double rr_hint = 32.0;        // running estimate of RR entries per sample
 };
 
 namespace fbpt {
 int workspace_release(fbpt_graph* g);
+// Builds g's out-edge CSR if it is not there yet (FBPT_EUNSUPPORTED for m >= 2^32).
+int ensure_out_csr(fbpt_graph* g, cudaStream_t st);
 // Device-wide exclusive scan of n counts into n+1 uint64 offsets (out[n] = total).
 int exclusive_scan_u32(const uint32_t* in, uint64_t* out, uint64_t n, cudaStream_t st);
 int exclusive_scan_u64(const uint64_t* in, uint64_t* out, uint64_t n, cudaStream_t st);

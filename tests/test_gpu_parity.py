@@ -183,3 +183,52 @@ def test_bad_options_rejected(fbpt, er_workload):
     rr = fbpt.sample(dg, 1, 0, 10)
     with pytest.raises(fbpt.FbptError):
         fbpt.select_seeds(rr, 2000)
+
+
+# ---- level schedules: push, filtered push, pull, heuristic, learned ----------------------------
+
+@pytest.fixture(scope="module")
+def rmat12_dense():
+    rp, col = synth.rmat_graph(12, 16, 78)
+    return synth.Graph(1 << 12, rp, col, synth.thr_uniform(col.size, 0.3), "rmat12-p0.3")
+
+
+def random_policy(fbpt, seed):
+    rng = np.random.default_rng(seed)
+    n = fbpt.lib().fbpt_policy_param_count()
+    p = rng.normal(0, 0.5, n).astype(np.float32)
+    p[:6] = rng.normal(10, 2, 6)
+    p[6:12] = rng.uniform(1, 4, 6)
+    return fbpt.Policy(p)
+
+
+@pytest.mark.parametrize("launch", ["host", "graph", "persistent"])
+@pytest.mark.parametrize("schedule", ["pull", "filtered", "heuristic", "learned"])
+@pytest.mark.parametrize("which", ["rmat12", "rmat12_dense"])
+def test_schedules_give_the_same_bits(fbpt, request, which, schedule, launch):
+    g = request.getfixturevalue(which)
+    dg = fbpt.Graph.from_synth(g)
+    policy = random_policy(fbpt, 5) if schedule == "learned" else None
+    ref = oracle.rr_sets(g, SEED, 11, 1500)
+    for words, slots, refill in ((4, 2, "lane"), (1, 1, "batch")):
+        rr = fbpt.sample(dg, SEED, 11, 1500, words=words, slots=slots, refill=refill, schedule=schedule,
+                         launch=launch, policy=policy)
+        assert_same(rr, ref, g)
+        if schedule == "pull":
+            assert rr.stats.pull_levels > 0 and rr.stats.push_levels == 0
+
+
+def test_heuristic_pulls_on_dense_frontiers(fbpt, rmat12_dense):
+    dg = fbpt.Graph.from_synth(rmat12_dense)
+    rr = fbpt.sample(dg, SEED, 0, 512, words=8, slots=1, refill="batch", schedule="heuristic", trace_cap=4096)
+    assert rr.stats.pull_levels > 0
+    assert set(np.unique(rr.trace["direction"])) <= {0, 1, 2}
+    assert_same(rr, oracle.rr_sets(rmat12_dense, SEED, 0, 512), rmat12_dense)
+
+
+def test_pull_limits(fbpt, rmat12):
+    dg = fbpt.Graph.from_synth(rmat12)
+    for kw in ({"words": 8, "slots": 8}, {"words": 1, "slots": 1, "unfused": True}):
+        with pytest.raises(fbpt.FbptError) as ei:
+            fbpt.sample(dg, 1, 0, 700, schedule="pull", **kw)
+        assert ei.value.code == fbpt.EUNSUPPORTED
