@@ -234,6 +234,26 @@ int fbpt_policy_create(const float* params, uint64_t count, fbpt_policy** out);
 int fbpt_policy_destroy(fbpt_policy* p);
 int fbpt_policy_get(const fbpt_policy* p, float* params, uint64_t count);
 
+/* Training on trace rows (host arrays): features[rows][6] as above,
+ * actions[rows] (the direction a level ran with), targets[rows] (its log2
+ * device time in ns).  Loss: mean of (out[action] - target)^2, full-batch
+ * Adam on the weights and biases for opts->steps steps (0 = 2000) at
+ * opts->lr (0 = 3e-3).  init_params may be NULL: the input mean and scale
+ * then come from the data and the weights from a seeded He initialisation.
+ * Forward, backward and update run in the library's own CUDA kernels.
+ * *out receives a new policy; *final_loss (may be NULL) its loss. */
+typedef struct fbpt_train_opts {
+    uint32_t steps;
+    float lr;
+    uint64_t seed;
+} fbpt_train_opts;
+int fbpt_policy_train(const float* features, const uint32_t* actions, const float* targets, uint64_t rows,
+                      const fbpt_train_opts* opts, const float* init_params, fbpt_policy** out, float* final_loss);
+/* Loss and gradient (param_count floats; zero for the input mean and scale)
+ * of the parameters on the rows, computed by the training kernel. */
+int fbpt_policy_loss_grad(const float* params, const float* features, const uint32_t* actions,
+                          const float* targets, uint64_t rows, float* loss, float* grad);
+
 /* ---- Building blocks exposed for verification ------------------------------------
  * Device results of the bit-level contract for given inputs (host arrays in
  * and out, count entries each): edge draws out[e & 3] for pairs (s[i], e[i]),

@@ -93,6 +93,11 @@ _SIGS = {
     "fbpt_policy_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_float), ctypes.c_uint64,
                                           ctypes.POINTER(ctypes.c_void_p)]),
     "fbpt_policy_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "fbpt_policy_train": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64,
+                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p),
+                                         ctypes.POINTER(ctypes.c_float)]),
+    "fbpt_policy_loss_grad": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_uint64, ctypes.POINTER(ctypes.c_float), ctypes.c_void_p]),
     "fbpt_policy_get": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float), ctypes.c_uint64]),
     "fbpt_last_error": (ctypes.c_char_p, []),
     "fbpt_version": (ctypes.c_int, []),
@@ -234,6 +239,8 @@ def make_opts(words=0, slots=0, schedule="push", launch="persistent", unfused=Fa
     o.schedule = SCHED[schedule] if isinstance(schedule, str) else int(schedule)
     o.launch = LAUNCH[launch] if isinstance(launch, str) else int(launch)
     o.unfused = int(bool(unfused))
+    if policy is None and o.schedule == SCHED["learned"]:
+        policy = default_policy()
     o.policy = policy._h.value if isinstance(policy, Policy) else policy
     o.stream = stream
     return o
@@ -316,6 +323,58 @@ class Policy:
             self.close()
         except Exception:
             pass
+
+
+DEFAULT_POLICY_FILE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "policy_default.txt")
+_default_policy = None
+
+
+def default_policy():
+    """The network shipped with the package (trained by train_policy.py on
+    per-level traces); the "learned" schedule uses it unless given another."""
+    global _default_policy
+    if _default_policy is None:
+        _default_policy = Policy(np.loadtxt(DEFAULT_POLICY_FILE, dtype=np.float64).astype(np.float32))
+    return _default_policy
+
+
+class TrainOpts(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_uint32), ("lr", ctypes.c_float), ("seed", ctypes.c_uint64)]
+
+
+def _train_arrays(features, actions, targets):
+    X = np.ascontiguousarray(features, np.float32).reshape(-1, 6)
+    A = np.ascontiguousarray(actions, np.uint32)
+    Y = np.ascontiguousarray(targets, np.float32)
+    if not (X.shape[0] == A.size == Y.size):
+        raise ValueError("features, actions and targets must have the same rows")
+    return X, A, Y
+
+
+def policy_train(features, actions, targets, steps=2000, lr=3e-3, seed=0, init=None):
+    """Train the schedule network on the GPU (fbpt_policy_train); returns (Policy, loss)."""
+    X, A, Y = _train_arrays(features, actions, targets)
+    o = TrainOpts(steps, lr, seed)
+    h = ctypes.c_void_p()
+    loss = ctypes.c_float()
+    init_arr = None if init is None else np.ascontiguousarray(init, np.float32)
+    _check(lib().fbpt_policy_train(X.ctypes.data, A.ctypes.data, Y.ctypes.data, X.shape[0], ctypes.addressof(o),
+                                   init_arr.ctypes.data if init_arr is not None else None, ctypes.byref(h),
+                                   ctypes.byref(loss)))
+    p = Policy.__new__(Policy)
+    p._h = h
+    return p, float(loss.value)
+
+
+def policy_loss_grad(params, features, actions, targets):
+    """(loss, gradient) of the parameters on the rows, from the GPU kernel."""
+    X, A, Y = _train_arrays(features, actions, targets)
+    P = np.ascontiguousarray(params, np.float32)
+    g = np.zeros(P.size, np.float32)
+    loss = ctypes.c_float()
+    _check(lib().fbpt_policy_loss_grad(P.ctypes.data, X.ctypes.data, A.ctypes.data, Y.ctypes.data, X.shape[0],
+                                       ctypes.byref(loss), g.ctypes.data))
+    return float(loss.value), g
 
 
 def edge_draws(seed: int, s, e):

@@ -1263,7 +1263,7 @@ int sample_impl(fbpt_graph* g, uint64_t seed, uint64_t first_id, uint64_t S, con
         FBPT_CUDA_TRY(cudaMallocAsync(&dtrace, sizeof(fbpt_trace_row) * o.trace_cap, st));
     Ctl* H = ws->ctl_host;
     int rc = FBPT_OK;
-    for (int attempt = 0; attempt < 3; ++attempt) {
+    for (int attempt = 0; attempt < 8; ++attempt) {
         if (pairs) cudaFreeAsync(pairs, st);
         FBPT_CUDA_TRY(cudaMallocAsync(&pairs, sizeof(uint64_t) * cap, st));
         FBPT_CUDA_TRY(cudaMemsetAsync(out->vcount, 0, sizeof(uint32_t) * g->n, st));
@@ -1330,6 +1330,18 @@ int sample_impl(fbpt_graph* g, uint64_t seed, uint64_t first_id, uint64_t S, con
         if (H->error & kErrBarrierTimeout) {
             rc = fail(FBPT_ETIMEOUT, "sampling run: a grid barrier wait gave up");
             break;
+        }
+        if (H->error == kErrSpillOverflow && ws->spill_cap < (1ull << 31)) {
+            // long RR sets outgrew the spill log: grow it and run again from a clean state
+            cudaStreamSynchronize(st);
+            cudaFree(ws->spill);
+            ws->spill = nullptr;
+            ws->spill_cap = std::min<uint64_t>(ws->spill_cap * 8, 1ull << 31);
+            size_t unused = 0;
+            FBPT_TRY(dalloc(&ws->spill, 2 * ws->spill_cap, unused));
+            FBPT_TRY(ws_zero(ws, st));
+            if (stats) stats->overflow_reruns += 1;
+            continue;
         }
         if (H->error) {
             rc = fail(FBPT_EDEVICE, "sampling run: device check failed (error bits " + std::to_string(H->error) + ")");

@@ -232,3 +232,17 @@ def test_pull_limits(fbpt, rmat12):
         with pytest.raises(fbpt.FbptError) as ei:
             fbpt.sample(dg, 1, 0, 700, schedule="pull", **kw)
         assert ei.value.code == fbpt.EUNSUPPORTED
+
+
+def test_long_rr_sets_grow_the_spill_log(fbpt):
+    """Supercritical uniform p: RR sets of ~n vertices overflow the lanes'
+    segments into the spill log, which grows (and the run repeats) until they
+    fit; the output stays exact."""
+    rp, col = synth.rmat_graph(14, 16, 93)
+    g = synth.Graph(1 << 14, rp, col, synth.thr_uniform(col.size, 0.3), "rmat14-p0.3")
+    dg = fbpt.Graph.from_synth(g)
+    rr = fbpt.sample(dg, SEED, 0, 2048, words=8, slots=4)
+    ref = oracle.rr_sets(g, SEED, 0, 2048)
+    assert np.diff(ref.offsets).max() > 1024
+    assert rr.stats.overflow_reruns >= 1
+    assert_same(rr, ref, g)
