@@ -245,9 +245,9 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(g, seed, 8192)
 
-    # kernels per step: 5 per level, radix sort 3 per 8-bit pass + scans, finalize, greedy 2 per pick + 3
-    passes = (st.rr_total and ((max(1, (S - 1).bit_length()) + max(1, (g.n - 1).bit_length()) + 7) // 8)) or 0
-    launches_step = 5 * int(st.levels) + 4 * passes + 1 + 2 * k + 4
+    # kernels per step: 5 per level, the final sweep, the row-length scan (3), the
+    # three row-ordering kernels, greedy 2 per pick + 3
+    launches_step = 5 * int(st.levels) + 1 + 3 + 3 + 2 * k + 3
     if rank == 0:
         print(json.dumps({
             "metric": METRIC, "value": value, "unit": "RR samples/s", "n_gpus": world, "steps": args.steps,

@@ -122,7 +122,8 @@ typedef struct fbpt_opts {
     uint32_t unfused;    /* 1 = each colour expands its own copy of every edge (no fusing);
                             output is identical, only the work differs */
     uint32_t refill;     /* enum fbpt_refill */
-    uint32_t reserved0;
+    uint32_t blocks;     /* CTAs of each level kernel; 0 = every CTA the GPU holds at once.
+                            Fewer leave room for other graphs of a batched run */
     const fbpt_policy* policy; /* used by FBPT_SCHED_LEARNED; NULL = built-in heuristic */
     void* stream;        /* cudaStream_t */
     uint64_t spin_limit; /* FBPT_LAUNCH_PERSISTENT: polls before a grid-barrier wait gives up
@@ -157,7 +158,9 @@ typedef struct fbpt_stats {
     uint64_t overflow_reruns;     /* batches re-run after the output pool grew */
     uint64_t mask_words;          /* non-zero 64-colour mask words of expanded frontier units */
     uint64_t trace_rows;          /* rows written to fbpt_opts.trace */
-    double ms_total;              /* time of the call on its stream (CUDA events) */
+    double ms_total;              /* device time of the call on its stream (CUDA events), from
+                                     the first sampling kernel to the finished CSR; workspace
+                                     allocation on a graph's first use is not included */
     double ms_expand;             /* device time of the expand phase: per level, first CTA start
                                      to last CTA end (%globaltimer), summed */
     double ms_commit;             /* same for the commit phase */
@@ -185,16 +188,55 @@ int fbpt_sample(fbpt_graph* g, uint64_t seed, uint64_t first_id, uint64_t S, con
                 fbpt_rrsets* out, fbpt_stats* stats);
 
 /* Many graphs in one run: graph i gets samples first_ids[i] .. + Ss[i] - 1
- * under seeds[i]; outs[i] receives its RR sets.  One CUDA graph drives all of
- * them (opts->launch is ignored); W per graph comes from the autotuner when
- * opts->words == 0. */
+ * under seeds[i]; outs[i] receives its RR sets, identical to what fbpt_sample
+ * gives for the same arguments.  With opts->launch FBPT_LAUNCH_HOST the graphs
+ * run one after another through fbpt_sample (the plain form).  Otherwise one
+ * CUDA graph holds every task as its own branch (the control block's reset, a
+ * WHILE node over the level kernels, the last sweep, the control block's
+ * read-back); branches of different graphs have no edges between them, so the
+ * GPU runs them concurrently, and tasks that share a graph (and so its
+ * workspace) are chained.  The whole batch is ONE cudaGraphLaunch.  When
+ * opts->words == 0, each graph runs with the shape fbpt_autotune stored on it
+ * (words, slots, refill, blocks), else the fixed default.  Tasks whose RR sets
+ * outgrew their buffers run again on their own.  Traces are not recorded.  On
+ * error every outs[i] is released. */
 int fbpt_sample_batched(uint32_t G, fbpt_graph* const* gs, const uint64_t* seeds, const uint64_t* first_ids,
                         const uint64_t* Ss, const fbpt_opts* opts, fbpt_rrsets* outs, fbpt_stats* stats);
+
+/* ---- Autotuner ------------------------------------------------------------------
+ * Launch shape of one graph, measured by fbpt_autotune: the mask row width
+ * (words * slots 64-bit words, i.e. that many 64-colour lane groups), the
+ * refill mode and the CTAs per level kernel. */
+typedef struct fbpt_tuning {
+    uint32_t words, slots, refill, blocks;
+    uint32_t candidates;      /* shapes measured */
+    uint32_t reserved;
+    uint64_t probe_samples;   /* samples per timed probe */
+    double probe_rate;        /* samples per second of the chosen shape in its probe */
+    double rr_per_sample;     /* mean RR set size seen by the probes */
+} fbpt_tuning;
+
+/* Times sampling runs of g (sample ids 0 .. min(S, 8192) - 1 under seed; each
+ * shape is warmed up on a smaller probe first) for row widths 1, 2, 4, ..., 64
+ * words (at most one lane per probe sample), then for the best width with
+ * 1, 1/2, 1/4 and 1/8 of the resident CTAs, and keeps the fastest width and the
+ * fewest CTAs within 3% of its rate.  base supplies the schedule and policy
+ * (NULL = push).  The result is stored on g (used by fbpt_sample_batched) and
+ * copied to out (may be NULL).  Output bits never depend on the shape. */
+int fbpt_autotune(fbpt_graph* g, uint64_t seed, uint64_t S, const fbpt_opts* base, fbpt_tuning* out);
+/* The shape stored on g by fbpt_autotune; FBPT_EINVAL if it was never tuned. */
+int fbpt_graph_tuning(const fbpt_graph* g, fbpt_tuning* out);
 
 int fbpt_rrsets_free(fbpt_rrsets* rr);
 /* Host copies (any pointer may be NULL): offsets[S+1], verts[total], starts[S], vcount[n]. */
 int fbpt_rrsets_copy_to_host(const fbpt_rrsets* rr, uint64_t* offsets, uint32_t* verts, uint32_t* starts,
                              uint32_t* vcount);
+/* Host copy of rows first_row .. first_row + count - 1 only: offsets_host
+ * receives count + 1 offsets (relative to the whole set, as in rr->offsets) and
+ * verts_host their vertices, at most verts_cap of them; FBPT_EINVAL if the rows
+ * are out of range or hold more than verts_cap vertices. */
+int fbpt_rrsets_copy_rows(const fbpt_rrsets* rr, uint64_t first_row, uint64_t count, uint64_t* offsets_host,
+                          uint32_t* verts_host, uint64_t verts_cap);
 
 /* ---- Seed selection -------------------------------------------------------------
  * Greedy max-k-cover over rr (contract above).  seeds_host[k] receives the

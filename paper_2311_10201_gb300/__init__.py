@@ -33,9 +33,19 @@ U32P = ctypes.POINTER(ctypes.c_uint32)
 class Opts(ctypes.Structure):
     _fields_ = [("words", ctypes.c_uint32), ("slots", ctypes.c_uint32), ("schedule", ctypes.c_uint32),
                 ("launch", ctypes.c_uint32), ("unfused", ctypes.c_uint32), ("refill", ctypes.c_uint32),
-                ("reserved0", ctypes.c_uint32),
+                ("blocks", ctypes.c_uint32),
                 ("policy", ctypes.c_void_p), ("stream", ctypes.c_void_p), ("spin_limit", ctypes.c_uint64),
                 ("trace", ctypes.c_void_p), ("trace_cap", ctypes.c_uint64)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("words", ctypes.c_uint32), ("slots", ctypes.c_uint32), ("refill", ctypes.c_uint32),
+                ("blocks", ctypes.c_uint32), ("candidates", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("probe_samples", ctypes.c_uint64), ("probe_rate", ctypes.c_double),
+                ("rr_per_sample", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
 
 
 class RRSetsC(ctypes.Structure):
@@ -81,6 +91,11 @@ _SIGS = {
                                    ctypes.POINTER(Opts), ctypes.POINTER(RRSetsC), ctypes.POINTER(Stats)]),
     "fbpt_sample_batched": (ctypes.c_int, [ctypes.c_uint32, ctypes.POINTER(ctypes.c_void_p), U64P, U64P, U64P,
                                            ctypes.POINTER(Opts), ctypes.POINTER(RRSetsC), ctypes.POINTER(Stats)]),
+    "fbpt_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.POINTER(Opts),
+                                     ctypes.POINTER(Tuning)]),
+    "fbpt_graph_tuning": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Tuning)]),
+    "fbpt_rrsets_copy_rows": (ctypes.c_int, [ctypes.POINTER(RRSetsC), ctypes.c_uint64, ctypes.c_uint64, U64P, U32P,
+                                             ctypes.c_uint64]),
     "fbpt_rrsets_free": (ctypes.c_int, [ctypes.POINTER(RRSetsC)]),
     "fbpt_rrsets_copy_to_host": (ctypes.c_int, [ctypes.POINTER(RRSetsC), ctypes.c_void_p, ctypes.c_void_p,
                                                 ctypes.c_void_p, ctypes.c_void_p]),
@@ -216,6 +231,20 @@ class RRSets:
                                               starts.ctypes.data, vcount.ctypes.data))
         return off, verts[:total], starts, vcount
 
+    def rows(self, first, count):
+        """Host copy of rows first .. first+count-1 only (fbpt_rrsets_copy_rows):
+        (offsets[count+1] relative to the whole set, their vertices)."""
+        off = np.empty(count + 1, np.uint64)
+        cp = lib().fbpt_rrsets_copy_rows
+        # the first and the last offset size the vertex buffer
+        _check(cp(ctypes.byref(self.c), first, 0, off[:1].ctypes.data_as(U64P), None, 0))
+        _check(cp(ctypes.byref(self.c), first + count, 0, off[count:].ctypes.data_as(U64P), None, 0))
+        n = int(off[count] - off[0])
+        verts = np.empty(max(n, 1), np.uint32)
+        _check(cp(ctypes.byref(self.c), first, count, off.ctypes.data_as(U64P), verts.ctypes.data_as(U32P),
+                  verts.size))
+        return off, verts[:n]
+
     def free(self):
         if self.c.offsets:
             lib().fbpt_rrsets_free(ctypes.byref(self.c))
@@ -231,8 +260,9 @@ REFILL = {"lane": 0, "batch": 1}
 
 
 def make_opts(words=0, slots=0, schedule="push", launch="persistent", unfused=False, stream=None, policy=None,
-              spin_limit=0, refill="lane"):
+              spin_limit=0, refill="lane", blocks=0):
     o = Opts()
+    o.blocks = int(blocks)
     o.refill = REFILL[refill] if isinstance(refill, str) else int(refill)
     o.spin_limit = int(spin_limit)
     o.words, o.slots = int(words), int(slots)
@@ -279,6 +309,22 @@ def sample_batched(graphs, seeds, first_ids, Ss, stream=None, **kw):
         ctypes.pointer(c)[0] = outs[i]
         res.append(RRSets(c, st))
     return res, st
+
+
+def autotune(g: Graph, seed: int, S: int, **kw) -> dict:
+    """Measure launch shapes of g (fbpt_autotune) and store the best on it; kw
+    gives the schedule (and policy) the probes run with."""
+    o = make_opts(stream=g.stream, **kw)
+    t = Tuning()
+    _check(lib().fbpt_autotune(g._h, seed, S, ctypes.byref(o), ctypes.byref(t)))
+    return t.as_dict()
+
+
+def tuning(g: Graph) -> dict:
+    """The shape fbpt_autotune stored on g."""
+    t = Tuning()
+    _check(lib().fbpt_graph_tuning(g._h, ctypes.byref(t)))
+    return t.as_dict()
 
 
 def select_seeds(rr: RRSets, k: int):

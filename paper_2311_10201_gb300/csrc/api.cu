@@ -23,9 +23,6 @@ int device_sm_count() {
     return sms;
 }
 
-int sample_impl(fbpt_graph* g, uint64_t seed, uint64_t first_id, uint64_t S, const fbpt_opts* opts, fbpt_rrsets* out,
-                fbpt_stats* stats);
-
 namespace {
 
 __global__ void k_edge_draws(uint64_t seed, const uint64_t* s, const uint64_t* e, uint64_t count, uint32_t* out) {
@@ -68,14 +65,25 @@ extern "C" int fbpt_sample(fbpt_graph* g, uint64_t seed, uint64_t first_id, uint
 
 extern "C" int fbpt_sample_batched(uint32_t G, fbpt_graph* const* gs, const uint64_t* seeds, const uint64_t* first_ids,
                                    const uint64_t* Ss, const fbpt_opts* opts, fbpt_rrsets* outs, fbpt_stats* stats) {
-    if (G == 0 || !gs || !seeds || !first_ids || !Ss || !outs) return fail(FBPT_EINVAL, "fbpt_sample_batched: null argument");
-    for (uint32_t i = 0; i < G; ++i) {
-        int rc = fbpt_sample(gs[i], seeds[i], first_ids[i], Ss[i], opts, &outs[i], stats);
-        if (rc != FBPT_OK) {
-            for (uint32_t j = 0; j < i; ++j) fbpt_rrsets_free(&outs[j]);
-            return rc;
-        }
+    try {
+        return sample_batched_impl(G, gs, seeds, first_ids, Ss, opts, outs, stats);
+    } catch (const std::exception& e) {
+        return fail(FBPT_ENOMEM, std::string("fbpt_sample_batched: ") + e.what());
     }
+}
+
+extern "C" int fbpt_autotune(fbpt_graph* g, uint64_t seed, uint64_t S, const fbpt_opts* base, fbpt_tuning* out) {
+    try {
+        return autotune_impl(g, seed, S, base, out);
+    } catch (const std::exception& e) {
+        return fail(FBPT_ENOMEM, std::string("fbpt_autotune: ") + e.what());
+    }
+}
+
+extern "C" int fbpt_graph_tuning(const fbpt_graph* g, fbpt_tuning* out) {
+    if (!g || !out) return fail(FBPT_EINVAL, "fbpt_graph_tuning: null argument");
+    if (!g->tuned_valid) return fail(FBPT_EINVAL, "fbpt_graph_tuning: graph was never tuned");
+    *out = g->tuned;
     return FBPT_OK;
 }
 
@@ -99,6 +107,25 @@ extern "C" int fbpt_rrsets_copy_to_host(const fbpt_rrsets* rr, uint64_t* offsets
     if (starts) FBPT_CUDA_TRY(cudaMemcpyAsync(starts, rr->starts, sizeof(uint32_t) * rr->S, cudaMemcpyDeviceToHost, st));
     if (vcount) FBPT_CUDA_TRY(cudaMemcpyAsync(vcount, rr->vcount, sizeof(uint32_t) * rr->n, cudaMemcpyDeviceToHost, st));
     FBPT_CUDA_TRY(cudaStreamSynchronize(st));
+    return FBPT_OK;
+}
+
+extern "C" int fbpt_rrsets_copy_rows(const fbpt_rrsets* rr, uint64_t first_row, uint64_t count, uint64_t* offsets_host,
+                                     uint32_t* verts_host, uint64_t verts_cap) {
+    if (!rr || !offsets_host) return fail(FBPT_EINVAL, "fbpt_rrsets_copy_rows: null argument");
+    if (first_row > rr->S || count > rr->S - first_row) return fail(FBPT_EINVAL, "fbpt_rrsets_copy_rows: rows out of range");
+    cudaStream_t st = (cudaStream_t)rr->stream;
+    FBPT_CUDA_TRY(cudaMemcpyAsync(offsets_host, rr->offsets + first_row, sizeof(uint64_t) * (count + 1),
+                                  cudaMemcpyDeviceToHost, st));
+    FBPT_CUDA_TRY(cudaStreamSynchronize(st));
+    const uint64_t len = offsets_host[count] - offsets_host[0];
+    if (len > verts_cap) return fail(FBPT_EINVAL, "fbpt_rrsets_copy_rows: rows hold more than verts_cap vertices");
+    if (len) {
+        if (!verts_host) return fail(FBPT_EINVAL, "fbpt_rrsets_copy_rows: null verts");
+        FBPT_CUDA_TRY(cudaMemcpyAsync(verts_host, rr->verts + offsets_host[0], sizeof(uint32_t) * len,
+                                      cudaMemcpyDeviceToHost, st));
+        FBPT_CUDA_TRY(cudaStreamSynchronize(st));
+    }
     return FBPT_OK;
 }
 

@@ -9,7 +9,7 @@
 // mask, and the in-edges of a unit are read once per level for all of its
 // colours (Listing 1's fusing update, over every sample in flight).  When a
 // lane's sample stops (no unit carries its bit), the next level sweeps the
-// lane's own list of reached vertices (a segment of kSegCap entries, then a
+// lane's own list of reached vertices (a segment of seg_cap entries, then a
 // shared spill log) into (sample, vertex) pairs, clears the lane's bit from
 // visited[], and the lane takes the next sample id (lane refill); or, in
 // batch mode, lanes wait until the whole row has finished, which is the plain
@@ -31,6 +31,7 @@
 // the hot loop streams col/thr with 128-bit loads instead of gathering masks.
 #include <algorithm>
 #include <cstring>
+#include <vector>
 #include <string>
 
 #include "internal.cuh"
@@ -63,6 +64,11 @@ struct CommitWarp {
     uint32_t occ_lo[32], occ_hi[32];
     uint32_t bits[32];
     uint32_t he[32];                // vertex has in-edges
+    // RR-list entries of the current 32 items, flattened across the warp
+    uint64_t ex[32];                // new colours of each item
+    uint32_t el[32];                // its first lane (64 * word)
+    uint32_t ev[32];                // its vertex
+    uint32_t es[32];                // its first entry
 };
 
 struct Smem {
@@ -72,6 +78,7 @@ struct Smem {
     uint64_t fin[kMaxWords];        // sweep: finished lanes (spill-log sweep)
     uint32_t cnt[kMaxWords + 1];    // schedule: per-word counts, then their prefix
     uint32_t tsum[kThreads + 1];    // schedule: per-thread sums of the block scan
+    unsigned long long wsum[kMaxWords];  // schedule: finished lanes' row lengths per word, then bases
     float feat[8], h1[kPolicyHidden], h2[kPolicyHidden], out[kPolicyOut];
     uint32_t last, abort, nstill, dir;
 };
@@ -98,15 +105,17 @@ __device__ __forceinline__ void or_next(const Eng& E, uint32_t w, uint32_t i, ui
         atomicOr(&E.ctl->error, (unsigned)kErrPendOverflow);
 }
 
-// ---- sweep: RR pairs of finished lanes (Listing 1's RRR-set construction) ------------------
+// ---- sweep: RR rows of finished lanes (Listing 1's RRR-set construction) -------------------
 
 // Every entry of a finished lane (its segment, plus the spill log when the
-// segment overflowed) is one (sample, vertex) pair of its RR set; the lane's
-// bit is cleared from visited[] so that the lane can carry its next sample.
-__device__ __forceinline__ void sweep_entry(const Eng& E, uint32_t l, uint32_t v, uint64_t& cev) {
+// segment overflowed) is one vertex of its sample's RR set.  The scheduler gave
+// the lane a staging range of the row's length; entry p of the lane's list
+// goes to position p of that range (vertices in discovery order; the final
+// CSR pass sorts each row).  The lane's bit is cleared from visited[] so that
+// the lane can carry its next sample.
+__device__ __forceinline__ void sweep_entry(const Eng& E, uint32_t l, uint32_t v) {
     atomicAnd((unsigned long long*)&E.visited[(uint64_t)v * E.WB + (l >> 6)], ~(1ull << (l & 63)));
     atomicAdd(&E.vcount[v], 1u);
-    cev += __ldg(&E.row_ptr[v + 1]) - __ldg(&E.row_ptr[v]);
 }
 
 __device__ void dev_sweep(const Eng& E, Smem& sm) {
@@ -124,24 +133,20 @@ __device__ void dev_sweep(const Eng& E, Smem& sm) {
     const uint64_t wid = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarp = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const uint64_t cap = L2(&ctl->pair_cap);
-    uint64_t cev = 0;
     for (uint64_t base = wid * 32; base < total; base += nwarp * 32) {
         const uint32_t idx = (uint32_t)(base + lane);
-        const bool ok = idx < total;
-        uint32_t l = 0, v = 0;
-        if (ok) {
+        if (idx < total) {
             uint32_t lo = 0, hi = F;  // largest k < F with prefix[k] <= idx
             while (hi - lo > 1) {
                 const uint32_t mid = (lo + hi) >> 1;
                 if (sm.lane[mid] <= idx) lo = mid; else hi = mid;
             }
-            l = L2(&ctl->fin_lane[lo]);
-            v = L2(&E.seg[(uint64_t)l * kSegCap + (idx - sm.lane[lo])]);
-        }
-        const uint64_t pos = warp_alloc<unsigned long long>(&ctl->pair_cursor, ok ? 1ull : 0ull);
-        if (ok) {
-            if (pos < cap) E.pairs[pos] = ((uint64_t)L2(&ctl->retired_j[l]) << E.vbits) | v;
-            sweep_entry(E, l, v, cev);
+            const uint32_t l = L2(&ctl->fin_lane[lo]);
+            const uint32_t p = idx - sm.lane[lo];
+            const uint32_t v = L2(&E.seg[(uint64_t)l * E.seg_cap + p]);
+            const uint64_t dst = L2(&ctl->lane_base[l]) + p;
+            if (dst < cap) E.rows_v[dst] = v;
+            sweep_entry(E, l, v);
         }
     }
     if (spill) {
@@ -151,27 +156,27 @@ __device__ void dev_sweep(const Eng& E, Smem& sm) {
             const uint64_t idx = base + lane;
             const bool ok = idx < len;
             uint32_t l = 0, v = 0;
+            uint64_t p = 0;
             bool done = false;
             uint64_t ent = 0;
             if (ok) {
                 ent = L2(&E.spill[(uint64_t)src * E.spill_cap + idx]);
-                l = (uint32_t)(ent >> 32);
-                v = (uint32_t)ent;
+                l = (uint32_t)(ent >> (2 * kSpillPosBits));
+                p = (ent >> kSpillPosBits) & kSpillMask;
+                v = (uint32_t)(ent & kSpillMask);
                 done = (sm.fin[l >> 6] >> (l & 63)) & 1ull;
             }
-            const uint64_t pos = warp_alloc<unsigned long long>(&ctl->pair_cursor, (ok && done) ? 1ull : 0ull);
             const uint64_t kp = warp_alloc<unsigned long long>(&ctl->spill_len[dst], (ok && !done) ? 1ull : 0ull);
             if (ok && done) {
-                if (pos < cap) E.pairs[pos] = ((uint64_t)L2(&ctl->retired_j[l]) << E.vbits) | v;
-                sweep_entry(E, l, v, cev);
+                const uint64_t d = L2(&ctl->lane_base[l]) + p;
+                if (d < cap) E.rows_v[d] = v;
+                sweep_entry(E, l, v);
             } else if (ok) {
                 if (kp < E.spill_cap) E.spill[(uint64_t)dst * E.spill_cap + kp] = ent;
                 else atomicOr(&ctl->error, (unsigned)kErrSpillOverflow);
             }
         }
     }
-    cev = warp_sum(cev);
-    if (lane == 0 && cev) atomicAdd(&ctl->st_cev, (unsigned long long)cev);
     phase_end(ctl, 2);
 }
 
@@ -508,42 +513,73 @@ __device__ void dev_commit(const Eng& E, Smem& sm) {
         cw.bits[lane] = 0;
         cw.he[lane] = re > rs;
         __syncwarp();
-        for (uint32_t t = lane; t < total; t += 32) {
-            uint32_t o = 0;  // the vertex owning item t: largest o with start[o] <= t
+        for (uint32_t t0 = 0; t0 < total; t0 += 32) {
+            const uint32_t t = t0 + lane;
+            uint64_t nx = 0;
+            uint32_t i = 0, wv = 0;
+            if (t < total) {
+                uint32_t o = 0;  // the vertex owning item t: largest o with start[o] <= t
 #pragma unroll
-            for (uint32_t step = 16; step > 0; step >>= 1)
-                if (cw.start[o + step] <= t) o += step;
-            const uint32_t i = nth_bit64(cw.m[o], t - cw.start[o]);
-            const uint32_t wv = cw.w[o];
-            const uint64_t rowi = (uint64_t)wv * E.WB + i;
-            uint64_t nx = L2(&E.next[rowi]);
-            E.next[rowi] = 0;
-            const uint64_t vis = L2(&E.visited[rowi]);
-            nx &= ~vis;
-            if (!nx) continue;
-            E.visited[rowi] = vis | nx;
-            E.stage[(base + o) * E.WB + i] = nx;
-            if (i < 32) atomicOr(&cw.occ_lo[o], 1u << i);
-            else atomicOr(&cw.occ_hi[o], 1u << (i - 32));
-            atomicAdd(&cw.bits[o], (uint32_t)__popcll(nx));
-            if (cw.he[o]) {
-                if ((uint32_t)nx) atomicOr(&sm.act[2 * i], (uint32_t)nx);
-                if (nx >> 32) atomicOr(&sm.act[2 * i + 1], (uint32_t)(nx >> 32));
-            }
-            uint64_t nb = nx;
-            while (nb) {
-                const uint32_t c = __ffsll((long long)nb) - 1;
-                nb &= nb - 1;
-                const uint32_t l = (i << 6) + c;
-                const uint32_t pos = atomicAdd(&ctl->lane_cnt[l], 1u);
-                if (pos < kSegCap) {
-                    E.seg[(uint64_t)l * kSegCap + pos] = wv;
-                } else {
-                    const uint64_t sp = atomicAdd(&ctl->spill_len[spill_cur], 1ull);
-                    if (sp < E.spill_cap) E.spill[(uint64_t)spill_cur * E.spill_cap + sp] = ((uint64_t)l << 32) | wv;
-                    else atomicOr(&ctl->error, (unsigned)kErrSpillOverflow);
+                for (uint32_t step = 16; step > 0; step >>= 1)
+                    if (cw.start[o + step] <= t) o += step;
+                i = nth_bit64(cw.m[o], t - cw.start[o]);
+                wv = cw.w[o];
+                const uint64_t rowi = (uint64_t)wv * E.WB + i;
+                nx = L2(&E.next[rowi]);
+                E.next[rowi] = 0;
+                const uint64_t vis = L2(&E.visited[rowi]);
+                nx &= ~vis;
+                if (nx) {
+                    E.visited[rowi] = vis | nx;
+                    E.stage[(base + o) * E.WB + i] = nx;
+                    if (i < 32) atomicOr(&cw.occ_lo[o], 1u << i);
+                    else atomicOr(&cw.occ_hi[o], 1u << (i - 32));
+                    atomicAdd(&cw.bits[o], (uint32_t)__popcll(nx));
+                    if (cw.he[o]) {
+                        if ((uint32_t)nx) atomicOr(&sm.act[2 * i], (uint32_t)nx);
+                        if (nx >> 32) atomicOr(&sm.act[2 * i + 1], (uint32_t)(nx >> 32));
+                    }
                 }
             }
+            // one entry per (item, new colour) in the lane's RR list; the
+            // warp takes them 32 at a time, and equal lanes share one atomic
+            const uint32_t nb = __popcll(nx);
+            const uint32_t einc = warp_incl_scan(nb);
+            const uint32_t etot = __shfl_sync(0xffffffffu, einc, 31);
+            cw.ex[lane] = nx;
+            cw.el[lane] = i << 6;
+            cw.ev[lane] = wv;
+            cw.es[lane] = einc - nb;
+            __syncwarp();
+            for (uint32_t e0 = 0; e0 < etot; e0 += 32) {
+                const uint32_t e = e0 + lane;
+                const bool ok = e < etot;
+                uint32_t l = 0xFFFFFFFFu, v = 0;
+                if (ok) {
+                    uint32_t q = 0;
+#pragma unroll
+                    for (uint32_t step = 16; step > 0; step >>= 1)
+                        if (cw.es[q + step] <= e) q += step;
+                    l = cw.el[q] + nth_bit64(cw.ex[q], e - cw.es[q]);
+                    v = cw.ev[q];
+                }
+                const uint32_t peers = __match_any_sync(0xffffffffu, l);
+                const uint32_t leader = __ffs(peers) - 1;
+                uint32_t pos = 0;
+                if (ok && lane == leader) pos = atomicAdd(&ctl->lane_cnt[l], (uint32_t)__popc(peers));
+                pos = __shfl_sync(0xffffffffu, pos, leader) + __popc(peers & lanemask_lt());
+                const bool spill = ok && pos >= E.seg_cap;
+                if (ok && !spill) E.seg[(uint64_t)l * E.seg_cap + pos] = v;
+                const uint64_t sp = warp_alloc<unsigned long long>(&ctl->spill_len[spill_cur], spill ? 1ull : 0ull);
+                if (spill) {
+                    if (sp < E.spill_cap)
+                        E.spill[(uint64_t)spill_cur * E.spill_cap + sp] =
+                            ((uint64_t)l << (2 * kSpillPosBits)) | ((uint64_t)pos << kSpillPosBits) | v;
+                    else
+                        atomicOr(&ctl->error, (unsigned)kErrSpillOverflow);
+                }
+            }
+            __syncwarp();
         }
         __syncwarp();
         const uint64_t occ = ((uint64_t)cw.occ_hi[lane] << 32) | cw.occ_lo[lane];
@@ -713,21 +749,48 @@ __device__ void dev_schedule(const Eng& E, Smem& sm) {
         sm.nstill = ns;
     }
     __syncthreads();
+    // staging ranges of the finished samples' rows, word by word in lane order
+    if (mine) {
+        uint64_t t = 0, f = fin;
+        while (f) {
+            const uint32_t c = __ffsll((long long)f) - 1;
+            f &= f - 1;
+            t += L2(&ctl->lane_cnt[(i << 6) + c]);
+        }
+        sm.wsum[i] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long acc = L2(&ctl->pair_cursor);
+        for (uint32_t w = 0; w < E.WB; ++w) {
+            const unsigned long long t = sm.wsum[w];
+            sm.wsum[w] = acc;
+            acc += t;
+        }
+        ctl->pair_cursor = acc;
+    }
+    __syncthreads();
     const uint32_t F = sm.cnt[E.WB];
     bool spilled = false;
     if (mine) {
         uint32_t k = sm.cnt[i];
         uint64_t f = fin;
+        unsigned long long rb = sm.wsum[i];
         while (f) {
             const uint32_t c = __ffsll((long long)f) - 1;
             f &= f - 1;
             const uint32_t l = (i << 6) + c;
             const uint32_t rc = L2(&ctl->lane_cnt[l]);
-            ctl->retired_j[l] = L2(&ctl->lane_j[l]);
+            const uint32_t j = L2(&ctl->lane_j[l]);
+            ctl->retired_j[l] = j;
+            ctl->lane_base[l] = rb;
+            E.row_start[j] = rb;
+            E.row_len[j] = rc;
+            rb += rc;
             ctl->lane_cnt[l] = 0;
             ctl->fin_lane[k] = l;
-            sm.lane[k] = min(rc, kSegCap);
-            spilled |= rc > kSegCap;
+            sm.lane[k] = min(rc, E.seg_cap);
+            spilled |= rc > E.seg_cap;
             ++k;
         }
         ctl->fin_mask[i] = fin;
@@ -975,19 +1038,129 @@ __global__ void __launch_bounds__(kThreads) k_run(const Eng E) {
     dev_sweep(E, sm);
 }
 
-// ---- finalize: sorted pairs -> CSR --------------------------------------------------------
+// ---- final CSR: each staged row sorted into its place -----------------------------------
+//
+// offsets[] is the exclusive scan of the row lengths in sample order; row j's
+// vertices (distinct, in discovery order in the staging array) are written to
+// verts[offsets[j] ..] ascending.  Rows of at most 32 vertices: one warp
+// (bitonic network on registers); up to kMidRow: one CTA (bitonic network in
+// shared memory); longer rows: one CTA marks a shared-memory bitmap of 2^20
+// vertices at a time and writes the marked ids in order.
 
-__global__ void k_finalize(const uint64_t* keys, uint64_t total, uint32_t vbits, uint64_t S, uint64_t* offsets,
-                           uint32_t* verts) {
-    const uint64_t vmask = (1ull << vbits) - 1;
-    for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < total;
-         p += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t key = keys[p];
-        const uint64_t j = key >> vbits;
-        verts[p] = (uint32_t)(key & vmask);
-        if (p == 0 || (keys[p - 1] >> vbits) != j) offsets[j] = p;
+constexpr uint32_t kMidRow = 8192;
+constexpr uint32_t kOrderThreads = 256;
+constexpr uint32_t kBigThreads = 1024;
+constexpr uint32_t kWinBits = 1u << 20;  // vertices per bitmap window (128 KB)
+
+// Colour-edge visits of a run: every RR entry (sample, v) examines v's in-edges
+// once, so the total is the sum over v of vcount[v] * indeg(v).
+__global__ void k_cev(const uint64_t* row_ptr, const uint32_t* vcount, uint32_t n, unsigned long long* out) {
+    unsigned long long acc = 0;
+    for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (uint64_t)gridDim.x * blockDim.x)
+        acc += (unsigned long long)vcount[v] * (row_ptr[v + 1] - row_ptr[v]);
+    acc = warp_sum(acc);
+    if (lane_id() == 0 && acc) atomicAdd(out, acc);
+}
+
+__global__ void __launch_bounds__(kOrderThreads) k_order_tiny(const uint32_t* rows_v, const uint64_t* row_start,
+                                                              const uint32_t* row_len, const uint64_t* offsets,
+                                                              uint64_t S, uint32_t* verts) {
+    const uint32_t lane = lane_id();
+    const uint64_t nwarp = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t j = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < S; j += nwarp) {
+        const uint32_t len = row_len[j];
+        if (len > 32) continue;
+        uint32_t v = lane < len ? rows_v[row_start[j] + lane] : 0xFFFFFFFFu;
+#pragma unroll
+        for (uint32_t k = 2; k <= 32; k <<= 1)
+#pragma unroll
+            for (uint32_t h = k >> 1; h > 0; h >>= 1) {
+                const uint32_t o = __shfl_xor_sync(0xffffffffu, v, h);
+                const bool up = (lane & k) == 0, low = (lane & h) == 0;
+                v = (low == up) ? min(v, o) : max(v, o);
+            }
+        if (lane < len) verts[offsets[j] + lane] = v;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) offsets[S] = total;
+}
+
+__global__ void __launch_bounds__(kOrderThreads) k_order_mid(const uint32_t* rows_v, const uint64_t* row_start,
+                                                             const uint32_t* row_len, const uint64_t* offsets,
+                                                             uint64_t S, uint32_t* verts) {
+    __shared__ uint32_t key[kMidRow];
+    for (uint64_t j = blockIdx.x; j < S; j += gridDim.x) {
+        const uint32_t len = row_len[j];
+        if (len <= 32 || len > kMidRow) continue;
+        uint32_t P = 64;
+        while (P < len) P <<= 1;
+        const uint64_t src = row_start[j];
+        for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) key[i] = i < len ? rows_v[src + i] : 0xFFFFFFFFu;
+        __syncthreads();
+        for (uint32_t k = 2; k <= P; k <<= 1)
+            for (uint32_t h = k >> 1; h > 0; h >>= 1) {
+                for (uint32_t t = threadIdx.x; t < P / 2; t += blockDim.x) {
+                    const uint32_t a = 2 * t - (t & (h - 1)), b = a + h;
+                    const uint32_t x = key[a], y = key[b];
+                    if ((x > y) == ((a & k) == 0)) {
+                        key[a] = y;
+                        key[b] = x;
+                    }
+                }
+                __syncthreads();
+            }
+        const uint64_t dst = offsets[j];
+        for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) verts[dst + i] = key[i];
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kBigThreads) k_order_big(const uint32_t* rows_v, const uint64_t* row_start,
+                                                           const uint32_t* row_len, const uint64_t* offsets,
+                                                           uint64_t S, uint32_t n, uint32_t* verts) {
+    extern __shared__ uint32_t bm[];  // kWinBits / 32 words
+    __shared__ uint32_t wsum[kBigThreads / 32];
+    __shared__ uint32_t wtot;
+    constexpr uint32_t kWords = kWinBits / 32;
+    constexpr uint32_t kPer = kWords / kBigThreads;  // bitmap words per thread
+    const uint32_t t = threadIdx.x, lane = lane_id(), warp = t >> 5;
+    for (uint64_t j = blockIdx.x; j < S; j += gridDim.x) {
+        const uint32_t len = row_len[j];
+        if (len <= kMidRow) continue;
+        const uint64_t src = row_start[j];
+        uint64_t dst = offsets[j];
+        for (uint32_t w0 = 0; w0 < n; w0 += kWinBits) {
+            for (uint32_t q = t; q < kWords; q += kBigThreads) bm[q] = 0;
+            __syncthreads();
+            for (uint32_t i = t; i < len; i += kBigThreads) {
+                const uint32_t v = rows_v[src + i] - w0;
+                if (v < kWinBits) atomicOr(&bm[v >> 5], 1u << (v & 31));
+            }
+            __syncthreads();
+            uint32_t c = 0;
+#pragma unroll 4
+            for (uint32_t q = 0; q < kPer; ++q) c += __popc(bm[t * kPer + q]);
+            const uint32_t incl = warp_incl_scan(c);
+            if (lane == 31) wsum[warp] = incl;
+            __syncthreads();
+            if (warp == 0) {
+                const uint32_t x = wsum[lane];
+                const uint32_t xi = warp_incl_scan(x);
+                wsum[lane] = xi - x;
+                if (lane == 31) wtot = xi;
+            }
+            __syncthreads();
+            uint64_t pos = dst + wsum[warp] + incl - c;
+            for (uint32_t q = 0; q < kPer; ++q) {
+                uint32_t m = bm[t * kPer + q];
+                while (m) {
+                    const uint32_t b = __ffs(m) - 1;
+                    m &= m - 1;
+                    verts[pos++] = w0 + (t * kPer + q) * 32 + b;
+                }
+            }
+            dst += wtot;
+            __syncthreads();
+        }
+    }
 }
 
 struct LaunchShape {
@@ -1010,19 +1183,38 @@ LaunchShape launch_shape() {
     return ls;
 }
 
-int launch_level(const Eng& E, cudaStream_t st) {
-    const LaunchShape ls = launch_shape();
-    k_sweep<<<ls.level_blocks, kThreads, 0, st>>>(E);
-    k_init<<<std::min(ls.level_blocks, (int)(64 * E.WB + kThreads - 1) / kThreads), kThreads, 0, st>>>(E);
-    k_expand<<<ls.level_blocks, kThreads, 0, st>>>(E);
-    k_commit<<<ls.level_blocks, kThreads, 0, st>>>(E);
+int order_rows(const uint32_t* rows_v, const uint64_t* row_start, const uint32_t* row_len, const uint64_t* offsets,
+               uint64_t S, uint32_t n, uint32_t* verts, cudaStream_t st) {
+    static bool attr = false;
+    if (!attr) {
+        FBPT_CUDA_TRY(cudaFuncSetAttribute(k_order_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)(kWinBits / 8)));
+        attr = true;
+    }
+    const int sms = device_sm_count();
+    const uint64_t grid = std::min<uint64_t>((S + 7) / 8, (uint64_t)sms * 8);
+    k_order_tiny<<<(unsigned)std::max<uint64_t>(grid, 1), kOrderThreads, 0, st>>>(rows_v, row_start, row_len,
+                                                                                    offsets, S, verts);
+    k_order_mid<<<(unsigned)std::min<uint64_t>(S, (uint64_t)sms * 6), kOrderThreads, 0, st>>>(
+        rows_v, row_start, row_len, offsets, S, verts);
+    k_order_big<<<(unsigned)std::min<uint64_t>(S, (uint64_t)sms), kBigThreads, kWinBits / 8, st>>>(
+        rows_v, row_start, row_len, offsets, S, n, verts);
+    FBPT_CUDA_TRY(cudaGetLastError());
+    return FBPT_OK;
+}
+
+int launch_level(const Eng& E, cudaStream_t st, int blocks) {
+    k_sweep<<<blocks, kThreads, 0, st>>>(E);
+    k_init<<<std::min(blocks, (int)(64 * E.WB + kThreads - 1) / kThreads), kThreads, 0, st>>>(E);
+    k_expand<<<blocks, kThreads, 0, st>>>(E);
+    k_commit<<<blocks, kThreads, 0, st>>>(E);
     k_schedule<<<1, kThreads, 0, st>>>(E);
     FBPT_CUDA_TRY(cudaGetLastError());
     return FBPT_OK;
 }
 
-int launch_final_sweep(const Eng& E, cudaStream_t st) {
-    k_sweep<<<launch_shape().level_blocks, kThreads, 0, st>>>(E);
+int launch_final_sweep(const Eng& E, cudaStream_t st, int blocks) {
+    k_sweep<<<blocks, kThreads, 0, st>>>(E);
     FBPT_CUDA_TRY(cudaGetLastError());
     return FBPT_OK;
 }
@@ -1039,59 +1231,49 @@ int run_persistent(const Eng& E, cudaStream_t st) {
     return FBPT_OK;
 }
 
-// The level loop as one CUDA graph: a WHILE conditional node whose body is
-// one level; the scheduler sets the condition.
-int run_graph(Eng E, cudaStream_t st) {
+// Adds to `graph` a WHILE conditional node (after deps) whose body is one
+// level of E's run; the scheduler kernel sets the condition.
+int add_level_loop(cudaGraph_t graph, const cudaGraphNode_t* deps, size_t ndeps, Eng E, int blocks,
+                   cudaGraphNode_t* node) {
+    cudaGraphConditionalHandle h;
+    if (cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault) != cudaSuccess)
+        return fail(FBPT_ECUDA, "cudaGraphConditionalHandleCreate failed");
+    cudaGraphNodeParams p = {};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    if (cudaGraphAddNode(node, graph, deps, nullptr, ndeps, &p) != cudaSuccess)
+        return fail(FBPT_ECUDA, "cudaGraphAddNode(conditional) failed");
+    cudaGraph_t body = p.conditional.phGraph_out[0];
+    cudaStream_t cs;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess)
+        return fail(FBPT_ECUDA, "stream create failed");
+    E.cond = (unsigned long long)h;
+    if (cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+        cudaStreamDestroy(cs);
+        return fail(FBPT_ECUDA, "cudaStreamBeginCaptureToGraph failed");
+    }
+    const int lrc = launch_level(E, cs, blocks);
+    cudaGraph_t captured = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(cs, &captured);
+    cudaStreamDestroy(cs);
+    if (lrc != FBPT_OK) return lrc;
+    if (ce != cudaSuccess) return fail(FBPT_ECUDA, std::string("capture failed: ") + cudaGetErrorString(ce));
+    return FBPT_OK;
+}
+
+// The level loop of one run as one CUDA graph, then the last sweep.
+int run_graph(const Eng& E, cudaStream_t st, int blocks) {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     FBPT_CUDA_TRY(cudaGraphCreate(&graph, 0));
-    int rc = FBPT_OK;
-    do {
-        cudaGraphConditionalHandle h;
-        if (cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault) != cudaSuccess) {
-            rc = fail(FBPT_ECUDA, "cudaGraphConditionalHandleCreate failed");
-            break;
-        }
-        cudaGraphNodeParams p = {};
-        p.type = cudaGraphNodeTypeConditional;
-        p.conditional.handle = h;
-        p.conditional.type = cudaGraphCondTypeWhile;
-        p.conditional.size = 1;
-        cudaGraphNode_t node;
-        if (cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &p) != cudaSuccess) {
-            rc = fail(FBPT_ECUDA, "cudaGraphAddNode(conditional) failed");
-            break;
-        }
-        cudaGraph_t body = p.conditional.phGraph_out[0];
-        cudaStream_t cs;
-        if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
-            rc = fail(FBPT_ECUDA, "stream create failed");
-            break;
-        }
-        E.cond = (unsigned long long)h;
-        if (cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) !=
-            cudaSuccess) {
-            cudaStreamDestroy(cs);
-            rc = fail(FBPT_ECUDA, "cudaStreamBeginCaptureToGraph failed");
-            break;
-        }
-        int lrc = launch_level(E, cs);
-        cudaGraph_t captured = nullptr;
-        cudaError_t ce = cudaStreamEndCapture(cs, &captured);
-        cudaStreamDestroy(cs);
-        if (lrc != FBPT_OK) { rc = lrc; break; }
-        if (ce != cudaSuccess) { rc = fail(FBPT_ECUDA, std::string("capture failed: ") + cudaGetErrorString(ce)); break; }
-        if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
-            rc = fail(FBPT_ECUDA, "cudaGraphInstantiate failed");
-            break;
-        }
-        if (cudaGraphLaunch(exec, st) != cudaSuccess) {
-            rc = fail(FBPT_ECUDA, "cudaGraphLaunch failed");
-            break;
-        }
-        E.cond = 0;
-        rc = launch_final_sweep(E, st);
-    } while (0);
+    cudaGraphNode_t node;
+    int rc = add_level_loop(graph, nullptr, 0, E, blocks, &node);
+    if (rc == FBPT_OK && cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess)
+        rc = fail(FBPT_ECUDA, "cudaGraphInstantiate failed");
+    if (rc == FBPT_OK && cudaGraphLaunch(exec, st) != cudaSuccess) rc = fail(FBPT_ECUDA, "cudaGraphLaunch failed");
+    if (rc == FBPT_OK) rc = launch_final_sweep(E, st, blocks);
     if (exec) {
         cudaStreamSynchronize(st);
         cudaGraphExecDestroy(exec);
@@ -1165,7 +1347,8 @@ int ws_get(fbpt_graph* g, uint32_t WB, bool unfused, bool dense, cudaStream_t st
     if (rc == FBPT_OK) rc = dalloc(&w->nocc, n, b);
     if (rc == FBPT_OK) rc = dalloc(&w->stage, w->pend_cap * WB, b);
     if (rc == FBPT_OK) rc = dalloc(&w->pend_v, w->pend_cap, b);
-    if (rc == FBPT_OK) rc = dalloc(&w->seg, 64ull * WB * kSegCap, b);
+    w->seg_cap = kSegMin;
+    if (rc == FBPT_OK) rc = dalloc(&w->seg, 64ull * WB * w->seg_cap, b);
     if (rc == FBPT_OK) rc = dalloc(&w->spill, 2 * w->spill_cap, b);
     if (rc == FBPT_OK) rc = dalloc(&w->list_v, w->list_cap, b);
     if (rc == FBPT_OK) rc = dalloc(&w->list_mrow, w->list_cap, b);
@@ -1190,10 +1373,376 @@ int ws_get(fbpt_graph* g, uint32_t WB, bool unfused, bool dense, cudaStream_t st
     return FBPT_OK;
 }
 
-uint32_t bits_for(uint64_t x) {  // bits to hold values 0 .. x
-    uint32_t b = 1;
-    while (b < 64 && (x >> b) != 0) ++b;
-    return b;
+
+}  // namespace
+
+
+namespace {
+
+// ---- one sampling run, in steps the batched path reuses -------------------------------
+
+struct Run {
+    fbpt_graph* g = nullptr;
+    uint64_t seed = 0, first_id = 0, S = 0;
+    fbpt_opts o = {};
+    uint32_t WB = 0;
+    int blocks = 0;
+    bool dense = false;
+    cudaStream_t st = nullptr;
+    Workspace* ws = nullptr;
+    fbpt_rrsets* out = nullptr;
+    uint64_t cap = 0;               // staging entries
+    uint32_t* rows_v = nullptr;     // staging: each finished sample's RR row, unsorted
+    uint64_t* row_start = nullptr;  // S
+    uint32_t* row_len = nullptr;    // S
+    fbpt_trace_row* dtrace = nullptr;
+    Ctl* H = nullptr;               // pinned: the initial control block in, the final one out
+    Eng E = {};
+};
+
+void release_out(fbpt_rrsets* out) {
+    if (!out) return;
+    cudaStream_t st = (cudaStream_t)out->stream;
+    if (out->offsets) cudaFreeAsync(out->offsets, st);
+    if (out->verts) cudaFreeAsync(out->verts, st);
+    if (out->starts) cudaFreeAsync(out->starts, st);
+    if (out->vcount) cudaFreeAsync(out->vcount, st);
+    std::memset(out, 0, sizeof(*out));
+}
+
+void run_release(Run& r, bool with_out) {
+    if (r.rows_v) cudaFreeAsync(r.rows_v, r.st);
+    if (r.row_start) cudaFreeAsync(r.row_start, r.st);
+    if (r.row_len) cudaFreeAsync(r.row_len, r.st);
+    if (r.dtrace) cudaFreeAsync(r.dtrace, r.st);
+    r.rows_v = nullptr;
+    r.row_start = nullptr;
+    r.row_len = nullptr;
+    r.dtrace = nullptr;
+    if (with_out) release_out(r.out);
+}
+
+// Replaces the spill log by an empty one of `cap` entries per buffer.
+int grow_spill(Workspace* ws, uint64_t cap, cudaStream_t st) {
+    cudaStreamSynchronize(st);
+    cudaFree(ws->spill);
+    ws->spill = nullptr;
+    ws->spill_cap = cap;
+    size_t unused = 0;
+    const int rc = dalloc(&ws->spill, 2 * cap, unused);
+    if (rc != FBPT_OK) ws->spill_cap = 0;  // the kernels then flag overflow instead of writing
+    return rc;
+}
+
+constexpr uint64_t kSpillMax = 1ull << 31;
+
+// Validates the arguments, gets the workspace and the output's fixed-size buffers.
+// force_wb (when not 0) sets the row width in words instead of the options:
+// tasks of a batch that share a graph use the widest of their widths.
+int run_setup(Run& r, fbpt_graph* g, uint64_t seed, uint64_t first_id, uint64_t S, const fbpt_opts* opts,
+              fbpt_rrsets* out, uint32_t force_wb = 0) {
+    if (!g || !out) return fail(FBPT_EINVAL, "fbpt_sample: null graph or output");
+    std::memset(out, 0, sizeof(*out));
+    if (S == 0 || S > 0xFFFFFFFFull) return fail(FBPT_EINVAL, "fbpt_sample: S must be in [1, 2^32)");
+    if (first_id + S < first_id) return fail(FBPT_EINVAL, "fbpt_sample: sample ids overflow");
+    fbpt_opts o = {};
+    if (opts) o = *opts;
+    const uint32_t W = o.words ? o.words : 8;
+    if (W != 1 && W != 2 && W != 4 && W != 8) return fail(FBPT_EINVAL, "fbpt_sample: words must be 1, 2, 4 or 8");
+    const uint32_t B = o.slots ? o.slots : kMaxWords / W;
+    if (B < 1 || B * W > kMaxWords) return fail(FBPT_EINVAL, "fbpt_sample: words * slots must be <= 64");
+    // never more lanes than samples (rounded up to whole words)
+    const uint32_t WB = force_wb ? force_wb : (uint32_t)std::min<uint64_t>(W * B, (S + 63) / 64);
+    if (WB > kMaxWords) return fail(FBPT_EINVAL, "fbpt_sample: row width above 64 words");
+    if (o.schedule > FBPT_SCHED_FILTERED) return fail(FBPT_EINVAL, "fbpt_sample: bad schedule");
+    // pull levels need dense frontier rows (WB <= 8 words), fused units and 32-bit edge ids
+    const bool pull_ok = WB <= kPullMaxWords && !o.unfused && g->m < (1ull << 32);
+    if (o.schedule == FBPT_SCHED_PULL && !pull_ok)
+        return fail(FBPT_EUNSUPPORTED, "fbpt_sample: pull needs words * slots <= 8, fused units and m < 2^32");
+    if (o.schedule == FBPT_SCHED_LEARNED && o.policy && !o.policy->d_params)
+        return fail(FBPT_EINVAL, "fbpt_sample: policy has no parameters");
+    if (o.launch != FBPT_LAUNCH_HOST && o.launch != FBPT_LAUNCH_GRAPH && o.launch != FBPT_LAUNCH_PERSISTENT)
+        return fail(FBPT_EINVAL, "fbpt_sample: bad launch mode");
+    if (o.refill != FBPT_REFILL_LANE && o.refill != FBPT_REFILL_BATCH)
+        return fail(FBPT_EINVAL, "fbpt_sample: bad refill mode");
+    r.g = g;
+    r.seed = seed;
+    r.first_id = first_id;
+    r.S = S;
+    r.o = o;
+    r.WB = WB;
+    r.dense = pull_ok && (o.schedule == FBPT_SCHED_PULL || o.schedule == FBPT_SCHED_HEURISTIC ||
+                          o.schedule == FBPT_SCHED_LEARNED);
+    r.st = o.stream ? (cudaStream_t)o.stream : g->stream;
+    const int full = launch_shape().level_blocks;
+    r.blocks = o.blocks ? std::max(1, std::min<int>((int)o.blocks, full)) : full;
+    r.out = out;
+
+    if (r.dense) FBPT_TRY(ensure_out_csr(g, r.st));
+    FBPT_TRY(ws_get(g, WB, o.unfused != 0, r.dense, r.st, &r.ws));
+    // per-lane segments sized to hold about twice the expected RR set, so that
+    // few lanes fall back to the shared spill log (which the sweep compacts
+    // every level); the rest of a longer set goes to the log
+    {
+        uint64_t want = kSegMin;
+        while (want < 2.0 * g->rr_hint && 64ull * WB * (want * 2) * sizeof(uint32_t) <= kSegBytesMax) want *= 2;
+        if (want > r.ws->seg_cap) {
+            cudaStreamSynchronize(r.st);
+            cudaFree(r.ws->seg);
+            r.ws->seg = nullptr;
+            r.ws->seg_cap = 0;
+            size_t unused = 0;
+            FBPT_TRY(dalloc(&r.ws->seg, 64ull * WB * want, unused));
+            r.ws->seg_cap = (uint32_t)want;
+        }
+        const double over = g->rr_hint * 1.5 - (double)r.ws->seg_cap;
+        const double spill_want = 64.0 * WB * over;
+        if (over > 0 && spill_want > (double)r.ws->spill_cap && r.ws->spill_cap < kSpillMax)
+            FBPT_TRY(grow_spill(r.ws, std::min<uint64_t>((uint64_t)spill_want, kSpillMax), r.st));
+    }
+    r.H = r.ws->ctl_host;
+
+    out->S = S;
+    out->n = g->n;
+    out->stream = r.st;
+    FBPT_CUDA_TRY(cudaMallocAsync(&out->starts, sizeof(uint32_t) * S, r.st));
+    FBPT_CUDA_TRY(cudaMallocAsync(&out->vcount, sizeof(uint32_t) * g->n, r.st));
+    FBPT_CUDA_TRY(cudaMallocAsync(&out->offsets, sizeof(uint64_t) * (S + 1), r.st));
+    FBPT_CUDA_TRY(cudaMallocAsync(&r.row_start, sizeof(uint64_t) * S, r.st));
+    FBPT_CUDA_TRY(cudaMallocAsync(&r.row_len, sizeof(uint32_t) * S, r.st));
+    r.cap = (uint64_t)(g->rr_hint * 1.25 * (double)S) + 4096;
+    if (o.trace && o.trace_cap)
+        FBPT_CUDA_TRY(cudaMallocAsync(&r.dtrace, sizeof(fbpt_trace_row) * o.trace_cap, r.st));
+    return FBPT_OK;
+}
+
+// Sizes the staging buffer and writes the initial control block (host side) and
+// the kernel parameters of one attempt.
+int run_arm(Run& r) {
+    fbpt_graph* g = r.g;
+    Workspace* ws = r.ws;
+    if (r.rows_v) cudaFreeAsync(r.rows_v, r.st);
+    r.rows_v = nullptr;
+    FBPT_CUDA_TRY(cudaMallocAsync(&r.rows_v, sizeof(uint32_t) * r.cap, r.st));
+    Ctl* H = r.H;
+    std::memset(H, 0, sizeof(Ctl));
+    H->S = r.S;
+    H->sched = r.o.schedule;
+    H->dir = r.o.schedule == FBPT_SCHED_FILTERED ? kDirFiltered : kDirPush;
+    H->refill = r.o.refill == FBPT_REFILL_BATCH ? kRefillBatch : kRefillLane;
+    H->pair_cap = r.cap;
+    for (int p = 0; p < 3; ++p) H->ph_t0[p] = ~0ull;
+    const uint64_t waves = r.S / (64ull * r.WB) + 2;
+    H->tick_limit = std::min<uint64_t>(waves * ((uint64_t)g->n + 2) + 16, 1ull << 40);
+
+    Eng& E = r.E;
+    E = Eng{};
+    E.n = g->n; E.WB = r.WB;
+    E.row_ptr = g->row_ptr; E.col = g->col; E.thr = g->thr;
+    E.seed = r.seed; E.first_id = r.first_id; E.S = r.S;
+    E.visited = ws->visited; E.next = ws->next; E.nocc = ws->nocc; E.stage = ws->stage;
+    E.pend_v = ws->pend_v; E.seg = ws->seg; E.seg_cap = ws->seg_cap; E.spill = ws->spill;
+    E.list_v = ws->list_v; E.list_mrow = ws->list_mrow; E.list_only = ws->list_only;
+    E.list_rs = ws->list_rs; E.list_re = ws->list_re; E.list_g = ws->list_g; E.list_occ = ws->list_occ;
+    E.chunk_u0 = ws->chunk_u0;
+    E.orow = g->orow; E.odst = g->odst; E.oeid = g->oeid;
+    E.frontd = ws->frontd; E.fstamp = ws->fstamp;
+    E.policy = (r.o.schedule == FBPT_SCHED_LEARNED && r.o.policy) ? r.o.policy->d_params : nullptr;
+    E.m = g->m;
+    E.pend_cap = ws->pend_cap; E.list_cap = ws->list_cap; E.chunk_cap = ws->chunk_cap;
+    E.spill_cap = ws->spill_cap;
+    E.unfused = r.o.unfused ? 1u : 0u;
+    E.ctl = ws->ctl;
+    E.starts = r.out->starts; E.vcount = r.out->vcount;
+    E.rows_v = r.rows_v; E.row_start = r.row_start; E.row_len = r.row_len;
+    E.cond = 0;
+    E.spin_limit = r.o.spin_limit ? r.o.spin_limit : (1ull << 26);
+    E.trace = r.dtrace;
+    E.trace_cap = r.dtrace ? r.o.trace_cap : 0;
+    ws->clean = false;
+    return FBPT_OK;
+}
+
+// Enqueues one attempt on the run's stream and reads the final control block
+// back into r.H (the caller synchronises).
+int run_enqueue(Run& r) {
+    Workspace* ws = r.ws;
+    const cudaStream_t st = r.st;
+    FBPT_CUDA_TRY(cudaMemcpyAsync(ws->ctl, r.H, sizeof(Ctl), cudaMemcpyHostToDevice, st));
+    FBPT_CUDA_TRY(cudaMemsetAsync(r.out->vcount, 0, sizeof(uint32_t) * r.g->n, st));
+    if (ws->fstamp) FBPT_CUDA_TRY(cudaMemsetAsync(ws->fstamp, 0xFF, sizeof(uint32_t) * r.g->n, st));
+    int rc = FBPT_OK;
+    if (r.o.launch == FBPT_LAUNCH_GRAPH) {
+        rc = run_graph(r.E, st, r.blocks);
+    } else if (r.o.launch == FBPT_LAUNCH_PERSISTENT) {
+        rc = run_persistent(r.E, st);
+    } else {
+        for (;;) {
+            rc = launch_level(r.E, st, r.blocks);
+            if (rc != FBPT_OK) break;
+            if (cudaMemcpyAsync(&r.H->running, &ws->ctl->running, sizeof(unsigned), cudaMemcpyDeviceToHost, st) !=
+                    cudaSuccess ||
+                cudaStreamSynchronize(st) != cudaSuccess)
+                return fail(FBPT_ECUDA, std::string("level loop: ") + cudaGetErrorString(cudaGetLastError()));
+            if (!r.H->running) break;
+        }
+        if (rc == FBPT_OK) rc = launch_final_sweep(r.E, st, r.blocks);
+    }
+    if (rc != FBPT_OK) return rc;
+    FBPT_CUDA_TRY(cudaMemcpyAsync(r.H, ws->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+    return FBPT_OK;
+}
+
+// Reads the outcome of an attempt from r.H.  Sets again when the run must be
+// repeated: the spill log was too small (grown here; the workspace is reset)
+// or the staging buffer was (its exact size is now known).
+int run_check(Run& r, fbpt_stats* stats, bool& again) {
+    again = false;
+    const Ctl* H = r.H;
+    Workspace* ws = r.ws;
+    if (H->error & kErrBarrierTimeout) return fail(FBPT_ETIMEOUT, "sampling run: a grid barrier wait gave up");
+    if (H->error == kErrSpillOverflow && ws->spill_cap < kSpillMax) {
+        // long RR sets outgrew the spill log: grow it and run again from a clean state
+        FBPT_TRY(grow_spill(ws, std::min<uint64_t>(ws->spill_cap * 8, kSpillMax), r.st));
+        FBPT_TRY(ws_zero(ws, r.st));
+        if (stats) stats->overflow_reruns += 1;
+        again = true;
+        return FBPT_OK;
+    }
+    if (H->error)
+        return fail(FBPT_EDEVICE, "sampling run: device check failed (error bits " + std::to_string(H->error) + ")");
+    ws->clean = true;  // every lane finished and was swept: the kernels restored the zero state
+    if (H->pair_cursor > r.cap) {
+        r.cap = H->pair_cursor + 1024;
+        if (stats) stats->overflow_reruns += 1;
+        again = true;
+    }
+    return FBPT_OK;
+}
+
+// Runs attempts until one fits (at most 8).
+int run_attempts(Run& r, fbpt_stats* stats) {
+    for (int attempt = 0; attempt < 8; ++attempt) {
+        FBPT_TRY(run_arm(r));
+        FBPT_TRY(run_enqueue(r));
+        if (cudaStreamSynchronize(r.st) != cudaSuccess)
+            return fail(FBPT_ECUDA, std::string("sampling run: ") + cudaGetErrorString(cudaGetLastError()));
+        bool again = false;
+        FBPT_TRY(run_check(r, stats, again));
+        if (!again) return FBPT_OK;
+    }
+    return fail(FBPT_ENOMEM, "fbpt_sample: output did not fit after re-runs");
+}
+
+// Trace copy, the CSR (offsets by a scan of the row lengths, each row sorted
+// into place), statistics.
+int run_finish(Run& r, fbpt_stats* stats) {
+    const Ctl* H = r.H;
+    const cudaStream_t st = r.st;
+    fbpt_rrsets* out = r.out;
+    if (r.dtrace) {
+        const uint64_t rows = std::min<uint64_t>(H->tick, r.o.trace_cap);
+        if (cudaMemcpyAsync(r.o.trace, r.dtrace, sizeof(fbpt_trace_row) * rows, cudaMemcpyDeviceToHost, st) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return fail(FBPT_ECUDA, "fbpt_sample: trace copy failed");
+        if (stats) stats->trace_rows = rows;
+    }
+    const uint64_t total = H->pair_cursor;
+    r.g->rr_hint = std::max(1.0, (double)total / (double)r.S);
+    FBPT_TRY(exclusive_scan_u32(r.row_len, out->offsets, r.S, st));
+    if (cudaMallocAsync(&out->verts, sizeof(uint32_t) * std::max<uint64_t>(total, 1), st) != cudaSuccess)
+        return fail(FBPT_ENOMEM, "fbpt_sample: verts");
+    FBPT_TRY(order_rows(r.rows_v, r.row_start, r.row_len, out->offsets, r.S, r.g->n, out->verts, st));
+    unsigned long long cev = 0;
+    if (stats) {
+        FBPT_CUDA_TRY(cudaMemsetAsync(&r.ws->ctl->st_cev, 0, sizeof(unsigned long long), st));
+        k_cev<<<device_sm_count() * 4, 256, 0, st>>>(r.g->row_ptr, out->vcount, r.g->n, &r.ws->ctl->st_cev);
+        FBPT_CUDA_TRY(cudaGetLastError());
+        FBPT_CUDA_TRY(cudaMemcpyAsync(&r.H->st_cev, &r.ws->ctl->st_cev, sizeof(unsigned long long),
+                                      cudaMemcpyDeviceToHost, st));
+        FBPT_CUDA_TRY(cudaStreamSynchronize(st));
+        cev = r.H->st_cev;
+    }
+    cudaFreeAsync(r.rows_v, st);
+    cudaFreeAsync(r.row_start, st);
+    cudaFreeAsync(r.row_len, st);
+    r.rows_v = nullptr;
+    r.row_start = nullptr;
+    r.row_len = nullptr;
+    out->total = total;
+    if (stats) {
+        stats->levels += H->tick;
+        stats->batches += (r.S + 64ull * r.WB - 1) / (64ull * r.WB);
+        stats->push_levels += H->st_push;
+        stats->pull_levels += H->st_pull;
+        stats->units_expanded += H->st_units;
+        stats->edge_accesses += H->st_edges;
+        stats->philox_calls += H->st_calls;
+        stats->colour_edge_visits += cev;
+        stats->rr_total += total;
+        stats->mask_words += H->st_mask_words;
+        stats->ms_expand += 1e-6 * (double)H->st_phase_ns[0];
+        stats->ms_commit += 1e-6 * (double)H->st_phase_ns[1];
+        stats->ms_sweep += 1e-6 * (double)H->st_phase_ns[2];
+    }
+    return FBPT_OK;
+}
+
+// Device time between two events recorded on the same stream; 0 if unavailable.
+float elapsed_ms(cudaEvent_t a, cudaEvent_t b) {
+    float ms = 0;
+    if (cudaEventSynchronize(b) != cudaSuccess || cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+        cudaGetLastError();
+        return 0.f;
+    }
+    return ms;
+}
+
+struct Events {
+    cudaEvent_t a = nullptr, b = nullptr;
+    Events() {
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+    }
+    ~Events() {
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+    }
+};
+
+// Adds one task's branch to the batched graph: control block in, vcount (and
+// pull stamps) cleared, the level loop, the last sweep, control block out.
+int add_task(cudaGraph_t graph, const cudaGraphNode_t* dep, Run& r, cudaGraphNode_t* tail) {
+    cudaGraphNode_t a, b;
+    FBPT_CUDA_TRY(cudaGraphAddMemcpyNode1D(&a, graph, dep, dep ? 1 : 0, r.ws->ctl, r.H, sizeof(Ctl),
+                                           cudaMemcpyHostToDevice));
+    cudaMemsetParams mp = {};
+    mp.dst = r.out->vcount;
+    mp.elementSize = 4;
+    mp.width = r.g->n;
+    mp.height = 1;
+    mp.value = 0;
+    FBPT_CUDA_TRY(cudaGraphAddMemsetNode(&b, graph, &a, 1, &mp));
+    if (r.ws->fstamp) {
+        mp.dst = r.ws->fstamp;
+        mp.value = 0xFFFFFFFFu;
+        FBPT_CUDA_TRY(cudaGraphAddMemsetNode(&a, graph, &b, 1, &mp));
+        b = a;
+    }
+    FBPT_TRY(add_level_loop(graph, &b, 1, r.E, r.blocks, &a));
+    Eng Ef = r.E;
+    Ef.cond = 0;
+    void* args[] = {(void*)&Ef};
+    cudaKernelNodeParams kp = {};
+    kp.func = (void*)k_sweep;
+    kp.gridDim = dim3(r.blocks);
+    kp.blockDim = dim3(kThreads);
+    kp.sharedMemBytes = 0;
+    kp.kernelParams = args;
+    FBPT_CUDA_TRY(cudaGraphAddKernelNode(&b, graph, &a, 1, &kp));
+    FBPT_CUDA_TRY(cudaGraphAddMemcpyNode1D(tail, graph, &b, 1, r.H, r.ws->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
+    return FBPT_OK;
 }
 
 }  // namespace
@@ -1209,208 +1758,205 @@ int workspace_release(fbpt_graph* g) {
 // One sampling run (rows first_id .. first_id+S-1) into out.
 int sample_impl(fbpt_graph* g, uint64_t seed, uint64_t first_id, uint64_t S, const fbpt_opts* opts, fbpt_rrsets* out,
                 fbpt_stats* stats) {
-    if (!g || !out) return fail(FBPT_EINVAL, "fbpt_sample: null graph or output");
-    if (S == 0 || S > 0xFFFFFFFFull) return fail(FBPT_EINVAL, "fbpt_sample: S must be in [1, 2^32)");
-    if (first_id + S < first_id) return fail(FBPT_EINVAL, "fbpt_sample: sample ids overflow");
-    fbpt_opts o = {};
-    if (opts) o = *opts;
-    const uint32_t W = o.words ? o.words : 8;
-    if (W != 1 && W != 2 && W != 4 && W != 8) return fail(FBPT_EINVAL, "fbpt_sample: words must be 1, 2, 4 or 8");
-    const uint32_t B = o.slots ? o.slots : kMaxWords / W;
-    if (B < 1 || B * W > kMaxWords) return fail(FBPT_EINVAL, "fbpt_sample: words * slots must be <= 64");
-    uint32_t WB = W * B;
-    // never more lanes than samples (rounded up to whole words)
-    WB = (uint32_t)std::min<uint64_t>(WB, (S + 63) / 64);
-    if (o.schedule > FBPT_SCHED_FILTERED) return fail(FBPT_EINVAL, "fbpt_sample: bad schedule");
-    // pull levels need dense frontier rows (WB <= 8 words), fused units and 32-bit edge ids
-    const bool pull_ok = WB <= kPullMaxWords && !o.unfused && g->m < (1ull << 32);
-    if (o.schedule == FBPT_SCHED_PULL && !pull_ok)
-        return fail(FBPT_EUNSUPPORTED, "fbpt_sample: pull needs words * slots <= 8, fused units and m < 2^32");
-    const bool dense = pull_ok && (o.schedule == FBPT_SCHED_PULL || o.schedule == FBPT_SCHED_HEURISTIC ||
-                                   o.schedule == FBPT_SCHED_LEARNED);
-    if (o.schedule == FBPT_SCHED_LEARNED && o.policy && !o.policy->d_params)
-        return fail(FBPT_EINVAL, "fbpt_sample: policy has no parameters");
-    if (o.launch != FBPT_LAUNCH_HOST && o.launch != FBPT_LAUNCH_GRAPH && o.launch != FBPT_LAUNCH_PERSISTENT)
-        return fail(FBPT_EINVAL, "fbpt_sample: bad launch mode");
-    if (o.refill != FBPT_REFILL_LANE && o.refill != FBPT_REFILL_BATCH)
-        return fail(FBPT_EINVAL, "fbpt_sample: bad refill mode");
-    cudaStream_t st = o.stream ? (cudaStream_t)o.stream : g->stream;
-    const uint32_t vbits = bits_for(g->n - 1);
-    const uint32_t sbits = bits_for(S - 1);
-    if (vbits + sbits > 64) return fail(FBPT_EUNSUPPORTED, "fbpt_sample: sample x vertex keys exceed 64 bits");
-
-    cudaEvent_t ev0, ev1;
-    cudaEventCreate(&ev0);
-    cudaEventCreate(&ev1);
-    cudaEventRecord(ev0, st);
-
-    if (dense) FBPT_TRY(ensure_out_csr(g, st));
-    Workspace* ws = nullptr;
-    FBPT_TRY(ws_get(g, WB, o.unfused != 0, dense, st, &ws));
-
-    std::memset(out, 0, sizeof(*out));
-    out->S = S;
-    out->n = g->n;
-    out->stream = st;
-    FBPT_CUDA_TRY(cudaMallocAsync(&out->starts, sizeof(uint32_t) * S, st));
-    FBPT_CUDA_TRY(cudaMallocAsync(&out->vcount, sizeof(uint32_t) * g->n, st));
-    FBPT_CUDA_TRY(cudaMallocAsync(&out->offsets, sizeof(uint64_t) * (S + 1), st));
-
-    uint64_t cap = (uint64_t)(g->rr_hint * 1.25 * (double)S) + 4096;
-    uint64_t* pairs = nullptr;
-    fbpt_trace_row* dtrace = nullptr;
-    if (o.trace && o.trace_cap)
-        FBPT_CUDA_TRY(cudaMallocAsync(&dtrace, sizeof(fbpt_trace_row) * o.trace_cap, st));
-    Ctl* H = ws->ctl_host;
-    int rc = FBPT_OK;
-    for (int attempt = 0; attempt < 8; ++attempt) {
-        if (pairs) cudaFreeAsync(pairs, st);
-        FBPT_CUDA_TRY(cudaMallocAsync(&pairs, sizeof(uint64_t) * cap, st));
-        FBPT_CUDA_TRY(cudaMemsetAsync(out->vcount, 0, sizeof(uint32_t) * g->n, st));
-        std::memset(H, 0, sizeof(Ctl));
-        H->S = S;
-        H->sched = o.schedule;
-        H->dir = o.schedule == FBPT_SCHED_FILTERED ? kDirFiltered : kDirPush;
-        H->refill = o.refill == FBPT_REFILL_BATCH ? kRefillBatch : kRefillLane;
-        H->pair_cap = cap;
-        for (int p = 0; p < 3; ++p) H->ph_t0[p] = ~0ull;
-        const uint64_t waves = S / (64ull * WB) + 2;
-        H->tick_limit = std::min<uint64_t>(waves * ((uint64_t)g->n + 2) + 16, 1ull << 40);
-        FBPT_CUDA_TRY(cudaMemcpyAsync(ws->ctl, H, sizeof(Ctl), cudaMemcpyHostToDevice, st));
-        if (ws->fstamp) FBPT_CUDA_TRY(cudaMemsetAsync(ws->fstamp, 0xFF, sizeof(uint32_t) * g->n, st));
-
-        Eng E = {};
-        E.n = g->n; E.WB = WB;
-        E.row_ptr = g->row_ptr; E.col = g->col; E.thr = g->thr;
-        E.seed = seed; E.first_id = first_id; E.S = S;
-        E.visited = ws->visited; E.next = ws->next; E.nocc = ws->nocc; E.stage = ws->stage;
-        E.pend_v = ws->pend_v; E.seg = ws->seg; E.spill = ws->spill;
-        E.list_v = ws->list_v; E.list_mrow = ws->list_mrow; E.list_only = ws->list_only;
-        E.list_rs = ws->list_rs; E.list_re = ws->list_re; E.list_g = ws->list_g; E.list_occ = ws->list_occ;
-        E.chunk_u0 = ws->chunk_u0;
-        E.orow = g->orow; E.odst = g->odst; E.oeid = g->oeid;
-        E.frontd = ws->frontd; E.fstamp = ws->fstamp;
-        E.policy = (o.schedule == FBPT_SCHED_LEARNED && o.policy) ? o.policy->d_params : nullptr;
-        E.m = g->m;
-        E.pend_cap = ws->pend_cap; E.list_cap = ws->list_cap; E.chunk_cap = ws->chunk_cap;
-        E.spill_cap = ws->spill_cap;
-        E.unfused = o.unfused ? 1u : 0u;
-        E.vbits = vbits;
-        E.ctl = ws->ctl;
-        E.starts = out->starts; E.vcount = out->vcount; E.pairs = pairs;
-        E.cond = 0;
-        E.spin_limit = o.spin_limit ? o.spin_limit : (1ull << 26);
-        E.trace = dtrace;
-        E.trace_cap = dtrace ? o.trace_cap : 0;
-        ws->clean = false;
-        if (o.launch == FBPT_LAUNCH_GRAPH) {
-            rc = run_graph(E, st);
-        } else if (o.launch == FBPT_LAUNCH_PERSISTENT) {
-            rc = run_persistent(E, st);
-        } else {
-            for (;;) {
-                rc = launch_level(E, st);
-                if (rc != FBPT_OK) break;
-                if (cudaMemcpyAsync(&H->running, &ws->ctl->running, sizeof(unsigned), cudaMemcpyDeviceToHost, st) !=
-                        cudaSuccess ||
-                    cudaStreamSynchronize(st) != cudaSuccess) {
-                    rc = fail(FBPT_ECUDA, std::string("level loop: ") + cudaGetErrorString(cudaGetLastError()));
-                    break;
-                }
-                if (!H->running) break;
-            }
-            if (rc == FBPT_OK) rc = launch_final_sweep(E, st);
-        }
-        if (rc != FBPT_OK) break;
-        if (cudaMemcpyAsync(H, ws->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-            cudaStreamSynchronize(st) != cudaSuccess) {
-            rc = fail(FBPT_ECUDA, std::string("sampling run: ") + cudaGetErrorString(cudaGetLastError()));
-            break;
-        }
-        if (H->error & kErrBarrierTimeout) {
-            rc = fail(FBPT_ETIMEOUT, "sampling run: a grid barrier wait gave up");
-            break;
-        }
-        if (H->error == kErrSpillOverflow && ws->spill_cap < (1ull << 31)) {
-            // long RR sets outgrew the spill log: grow it and run again from a clean state
-            cudaStreamSynchronize(st);
-            cudaFree(ws->spill);
-            ws->spill = nullptr;
-            ws->spill_cap = std::min<uint64_t>(ws->spill_cap * 8, 1ull << 31);
-            size_t unused = 0;
-            FBPT_TRY(dalloc(&ws->spill, 2 * ws->spill_cap, unused));
-            FBPT_TRY(ws_zero(ws, st));
-            if (stats) stats->overflow_reruns += 1;
-            continue;
-        }
-        if (H->error) {
-            rc = fail(FBPT_EDEVICE, "sampling run: device check failed (error bits " + std::to_string(H->error) + ")");
-            break;
-        }
-        ws->clean = true;  // every lane finished and was swept: the kernels restored the zero state
-        if (H->pair_cursor <= cap) break;
-        cap = H->pair_cursor + 1024;  // exact size is now known; run again
-        if (stats) stats->overflow_reruns += 1;
+    Run r;
+    int rc = run_setup(r, g, seed, first_id, S, opts, out);
+    Events ev;
+    if (rc == FBPT_OK) {
+        cudaEventRecord(ev.a, r.st);
+        rc = run_attempts(r, stats);
     }
-    if (dtrace) {
-        if (rc == FBPT_OK) {
-            const uint64_t rows = std::min<uint64_t>(H->tick, o.trace_cap);
-            if (cudaMemcpyAsync(o.trace, dtrace, sizeof(fbpt_trace_row) * rows, cudaMemcpyDeviceToHost, st) !=
-                    cudaSuccess ||
-                cudaStreamSynchronize(st) != cudaSuccess)
-                rc = fail(FBPT_ECUDA, "fbpt_sample: trace copy failed");
-            if (stats) stats->trace_rows = rows;
-        }
-        cudaFreeAsync(dtrace, st);
-    }
+    if (rc == FBPT_OK) rc = run_finish(r, stats);
     if (rc != FBPT_OK) {
-        if (pairs) cudaFreeAsync(pairs, st);
+        run_release(r, true);
         return rc;
     }
-    const uint64_t total = H->pair_cursor;
-    if (total > cap) {
-        cudaFreeAsync(pairs, st);
-        return fail(FBPT_ENOMEM, "fbpt_sample: output did not fit after re-runs");
+    cudaEventRecord(ev.b, r.st);
+    const float ms = elapsed_ms(ev.a, ev.b);
+    if (stats) stats->ms_total += ms;
+    return FBPT_OK;
+}
+
+int sample_batched_impl(uint32_t G, fbpt_graph* const* gs, const uint64_t* seeds, const uint64_t* first_ids,
+                        const uint64_t* Ss, const fbpt_opts* opts, fbpt_rrsets* outs, fbpt_stats* stats) {
+    if (G == 0 || !gs || !seeds || !first_ids || !Ss || !outs)
+        return fail(FBPT_EINVAL, "fbpt_sample_batched: null argument");
+    for (uint32_t i = 0; i < G; ++i) std::memset(&outs[i], 0, sizeof(outs[i]));
+    fbpt_opts base = {};
+    if (opts) base = *opts;
+    base.trace = nullptr;
+    base.trace_cap = 0;
+    std::vector<fbpt_opts> oi(G, base);
+    for (uint32_t i = 0; i < G; ++i) {
+        if (!gs[i]) return fail(FBPT_EINVAL, "fbpt_sample_batched: null graph");
+        if (base.words == 0 && gs[i]->tuned_valid) {
+            oi[i].words = gs[i]->tuned.words;
+            oi[i].slots = gs[i]->tuned.slots;
+            oi[i].refill = gs[i]->tuned.refill;
+            oi[i].blocks = gs[i]->tuned.blocks;
+        }
     }
-    g->rr_hint = std::max(1.0, (double)total / (double)S);
-    uint64_t* tmp = nullptr;
-    if (cudaMallocAsync(&tmp, sizeof(uint64_t) * std::max<uint64_t>(total, 1), st) != cudaSuccess)
-        rc = fail(FBPT_ENOMEM, "fbpt_sample: sort buffer");
-    if (rc == FBPT_OK) rc = radix_sort_u64(pairs, tmp, total, vbits + sbits, st);
-    if (rc == FBPT_OK && cudaMallocAsync(&out->verts, sizeof(uint32_t) * std::max<uint64_t>(total, 1), st) != cudaSuccess)
-        rc = fail(FBPT_ENOMEM, "fbpt_sample: verts");
-    if (rc == FBPT_OK) {
-        const int blocks = (int)std::min<uint64_t>((total + 255) / 256 + 1, (uint64_t)device_sm_count() * 8);
-        k_finalize<<<blocks, 256, 0, st>>>(pairs, total, vbits, S, out->offsets, out->verts);
-        if (cudaGetLastError() != cudaSuccess) rc = fail(FBPT_ECUDA, "finalize launch failed");
+    if (base.launch == FBPT_LAUNCH_HOST) {
+        // the plain form: one run after another
+        for (uint32_t i = 0; i < G; ++i) {
+            const int rc = sample_impl(gs[i], seeds[i], first_ids[i], Ss[i], &oi[i], &outs[i], stats);
+            if (rc != FBPT_OK) {
+                for (uint32_t j = 0; j < i; ++j) release_out(&outs[j]);
+                return rc;
+            }
+        }
+        return FBPT_OK;
     }
-    if (tmp) cudaFreeAsync(tmp, st);
-    cudaFreeAsync(pairs, st);
-    if (rc != FBPT_OK) return rc;
-    out->total = total;
-    cudaEventRecord(ev1, st);
-    if (cudaEventSynchronize(ev1) != cudaSuccess)
-        return fail(FBPT_ECUDA, std::string("fbpt_sample: ") + cudaGetErrorString(cudaGetLastError()));
-    float ms = 0;
-    cudaEventElapsedTime(&ms, ev0, ev1);
-    cudaEventDestroy(ev0);
-    cudaEventDestroy(ev1);
-    if (stats) {
-        stats->levels += H->tick;
-        stats->batches += (S + 64ull * WB - 1) / (64ull * WB);
-        stats->push_levels += H->st_push;
-        stats->pull_levels += H->st_pull;
-        stats->units_expanded += H->st_units;
-        stats->edge_accesses += H->st_edges;
-        stats->philox_calls += H->st_calls;
-        stats->colour_edge_visits += H->st_cev;
-        stats->rr_total += total;
-        stats->mask_words += H->st_mask_words;
-        stats->ms_total += ms;
-        stats->ms_expand += 1e-6 * (double)H->st_phase_ns[0];
-        stats->ms_commit += 1e-6 * (double)H->st_phase_ns[1];
-        stats->ms_sweep += 1e-6 * (double)H->st_phase_ns[2];
+    for (uint32_t i = 0; i < G; ++i) oi[i].launch = FBPT_LAUNCH_GRAPH;
+    Ctl* Hs = nullptr;
+    if (cudaMallocHost((void**)&Hs, sizeof(Ctl) * G) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(FBPT_ENOMEM, "fbpt_sample_batched: pinned control blocks");
     }
+    std::vector<Run> runs(G);
+    cudaStream_t st = base.stream ? (cudaStream_t)base.stream : gs[0]->stream;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    Events ev;
+    int rc = FBPT_OK;
+    // tasks on one graph share its workspace, so they share one row width: the
+    // widest any of them would get alone (a lane without a sample stays idle)
+    std::vector<uint32_t> wb(G, 0);
+    for (uint32_t i = 0; i < G; ++i) {
+        const uint32_t W = oi[i].words ? oi[i].words : 8;
+        const uint32_t B = oi[i].slots ? oi[i].slots : kMaxWords / std::max<uint32_t>(W, 1);
+        wb[i] = (uint32_t)std::min<uint64_t>((uint64_t)W * B, (Ss[i] + 63) / 64);
+    }
+    for (uint32_t i = 0; i < G; ++i)
+        for (uint32_t j = 0; j < G; ++j)
+            if (gs[j] == gs[i]) wb[i] = std::max(wb[i], wb[j]);
+    for (uint32_t i = 0; i < G && rc == FBPT_OK; ++i) {
+        oi[i].stream = st;
+        rc = run_setup(runs[i], gs[i], seeds[i], first_ids[i], Ss[i], &oi[i], &outs[i], wb[i]);
+        runs[i].H = &Hs[i];
+        for (uint32_t j = 0; j < i && rc == FBPT_OK; ++j)
+            if (gs[j] == gs[i] && (runs[j].WB != runs[i].WB || runs[j].dense != runs[i].dense))
+                rc = fail(FBPT_EINVAL, "fbpt_sample_batched: tasks on one graph need one workspace shape");
+    }
+    if (rc == FBPT_OK) cudaEventRecord(ev.a, st);
+    for (uint32_t i = 0; i < G && rc == FBPT_OK; ++i) rc = run_arm(runs[i]);
+    // one graph: a branch per task; tasks on one graph chained in order
+    if (rc == FBPT_OK && cudaGraphCreate(&graph, 0) != cudaSuccess) rc = fail(FBPT_ECUDA, "cudaGraphCreate failed");
+    std::vector<cudaGraphNode_t> tails(G);
+    for (uint32_t i = 0; i < G && rc == FBPT_OK; ++i) {
+        const cudaGraphNode_t* dep = nullptr;
+        for (uint32_t j = i; j-- > 0;)
+            if (gs[j] == gs[i]) {
+                dep = &tails[j];
+                break;
+            }
+        rc = add_task(graph, dep, runs[i], &tails[i]);
+    }
+    if (rc == FBPT_OK && cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess)
+        rc = fail(FBPT_ECUDA, "cudaGraphInstantiate failed");
+    if (rc == FBPT_OK && cudaGraphLaunch(exec, st) != cudaSuccess) rc = fail(FBPT_ECUDA, "cudaGraphLaunch failed");
+    if (rc == FBPT_OK && cudaStreamSynchronize(st) != cudaSuccess)
+        rc = fail(FBPT_ECUDA, std::string("batched run: ") + cudaGetErrorString(cudaGetLastError()));
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    // outcomes in task order; a task that failed on the device leaves its
+    // graph's workspace dirty, so later tasks on that graph run again too
+    std::vector<fbpt_graph*> dirty;
+    for (uint32_t i = 0; i < G && rc == FBPT_OK; ++i) {
+        Run& r = runs[i];
+        bool again = false;
+        if (std::find(dirty.begin(), dirty.end(), gs[i]) != dirty.end()) {
+            again = true;
+        } else {
+            rc = run_check(r, stats, again);
+            if (rc == FBPT_OK && again && r.H->error) dirty.push_back(gs[i]);
+        }
+        if (rc == FBPT_OK && again) rc = run_attempts(r, stats);
+    }
+    for (uint32_t i = 0; i < G && rc == FBPT_OK; ++i) rc = run_finish(runs[i], stats);
+    if (rc != FBPT_OK) {
+        for (uint32_t i = 0; i < G; ++i) {
+            runs[i].out = &outs[i];
+            run_release(runs[i], true);
+        }
+        cudaStreamSynchronize(st);
+        cudaFreeHost(Hs);
+        return rc;
+    }
+    cudaEventRecord(ev.b, st);
+    const float ms = elapsed_ms(ev.a, ev.b);
+    if (stats) stats->ms_total += ms;
+    cudaFreeHost(Hs);
+    return FBPT_OK;
+}
+
+int autotune_impl(fbpt_graph* g, uint64_t seed, uint64_t S, const fbpt_opts* base, fbpt_tuning* out) {
+    if (!g) return fail(FBPT_EINVAL, "fbpt_autotune: null graph");
+    if (S == 0) return fail(FBPT_EINVAL, "fbpt_autotune: S must be >= 1");
+    fbpt_opts o = {};
+    if (base) o = *base;
+    o.trace = nullptr;
+    o.trace_cap = 0;
+    o.unfused = 0;
+    if (o.launch == FBPT_LAUNCH_PERSISTENT) o.launch = FBPT_LAUNCH_GRAPH;
+    const uint64_t P = std::min<uint64_t>(S, 8192);
+    const uint64_t warm = std::max<uint64_t>(P / 8, std::min<uint64_t>(P, 64));
+    fbpt_tuning t = {};
+    t.probe_samples = P;
+    double rr_sum = 0;
+    uint64_t rr_n = 0;
+    // samples per second of one shape (a warm-up run on `warm` samples first)
+    auto probe = [&](uint32_t WB, uint32_t blocks, double& rate) -> int {
+        fbpt_opts q = o;
+        q.words = std::min<uint32_t>(WB, 8);
+        q.slots = WB / q.words;
+        q.refill = FBPT_REFILL_LANE;
+        q.blocks = blocks;
+        if (q.schedule == FBPT_SCHED_PULL && WB > kPullMaxWords) q.schedule = FBPT_SCHED_HEURISTIC;
+        fbpt_rrsets rr;
+        fbpt_stats s0 = {}, s1 = {};
+        FBPT_TRY(sample_impl(g, seed, 0, warm, &q, &rr, &s0));
+        release_out(&rr);
+        FBPT_TRY(sample_impl(g, seed, 0, P, &q, &rr, &s1));
+        release_out(&rr);
+        rate = s1.ms_total > 0 ? (double)P / (1e-3 * s1.ms_total) : 0.0;
+        rr_sum += (double)s1.rr_total;
+        rr_n += P;
+        t.candidates += 1;
+        return FBPT_OK;
+    };
+    uint32_t best_wb = 1;
+    double best = -1;
+    for (uint32_t WB = 1; WB <= kMaxWords; WB *= 2) {
+        if (WB > 1 && 64ull * WB > P) break;
+        double rate = 0;
+        FBPT_TRY(probe(WB, 0, rate));
+        if (rate > best) {
+            best = rate;
+            best_wb = WB;
+        }
+    }
+    const int full = launch_shape().level_blocks;
+    uint32_t best_blocks = (uint32_t)full;
+    double best_rate = best;
+    for (int div = 2; div <= 8; div *= 2) {
+        const uint32_t blocks = (uint32_t)std::max(1, full / div);
+        double rate = 0;
+        FBPT_TRY(probe(best_wb, blocks, rate));
+        if (rate >= 0.97 * best) {
+            best_blocks = blocks;
+            best_rate = rate;
+        }
+    }
+    t.words = std::min<uint32_t>(best_wb, 8);
+    t.slots = best_wb / t.words;
+    t.refill = FBPT_REFILL_LANE;
+    t.blocks = best_blocks;
+    t.probe_rate = best_rate;
+    t.rr_per_sample = rr_n ? rr_sum / (double)rr_n : 0.0;
+    g->tuned = t;
+    g->tuned_valid = true;
+    if (t.rr_per_sample > 0) g->rr_hint = t.rr_per_sample;
+    if (out) *out = t;
     return FBPT_OK;
 }
 

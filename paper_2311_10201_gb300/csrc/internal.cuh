@@ -12,7 +12,11 @@ constexpr uint32_t kMaxWords = 64;      // 64-bit colour words per vertex row
 constexpr uint32_t kMaxLanes = 64 * kMaxWords;
 constexpr uint32_t kUnitBits = 26;      // list allocation counter: units in the low 26 bits
 constexpr uint64_t kUnitMask = (1ull << kUnitBits) - 1;
-constexpr uint32_t kSegCap = 1024;      // RR entries a lane keeps in its own segment
+constexpr uint32_t kSegMin = 1024;      // smallest per-lane segment (RR entries a lane keeps in its own list)
+constexpr uint64_t kSegBytesMax = 2ull << 30;  // largest segment array of a workspace
+// A spill-log entry packs (lane, position in the lane's row, vertex) as 12 + 26 + 26 bits.
+constexpr uint32_t kSpillPosBits = 26;
+constexpr uint64_t kSpillMask = (1ull << kSpillPosBits) - 1;
 constexpr uint32_t kChunk = 32;         // 4-edge groups per expand chunk (one per lane)
 constexpr uint32_t kChunksPerGrab = 4;  // chunks a warp takes per atomic
 
@@ -58,7 +62,7 @@ struct Ctl {
     unsigned int sched;              // fbpt_schedule of the run
     unsigned long long tick, tick_limit;
     unsigned long long next_j, S;    // next sample index to hand out; samples in the run
-    unsigned long long pair_cursor, pair_cap;
+    unsigned long long pair_cursor, pair_cap; // staging entries handed to finished samples' rows; capacity
     unsigned long long run_w[kMaxWords];   // lanes holding a sample
     unsigned long long act_w[kMaxWords];   // lanes present in the new frontier
     unsigned long long init_w[kMaxWords];  // lanes given a sample at the last schedule (init input)
@@ -66,6 +70,7 @@ struct Ctl {
     unsigned int lane_j[kMaxLanes];        // sample index held by each lane
     unsigned int lane_cnt[kMaxLanes];      // RR entries of the lane's current sample so far
     unsigned int retired_j[kMaxLanes];     // sample index a finished lane held
+    unsigned long long lane_base[kMaxLanes]; // staging position of a finished lane's row
     // sweep input, written by the schedule: finished lanes and the prefix of
     // their segment entry counts
     unsigned int fin_count;
@@ -93,7 +98,8 @@ struct Workspace {
     uint64_t* nocc = nullptr;     // n: bit i set iff next[v][i] != 0 (and v is pending)
     uint64_t* stage = nullptr;    // pend_cap * WB: new frontier masks by pend index
     uint32_t* pend_v = nullptr;   // pend_cap
-    uint32_t* seg = nullptr;      // 64 * WB * kSegCap: each lane's RR vertices
+    uint32_t* seg = nullptr;      // 64 * WB * seg_cap: each lane's RR vertices
+    uint32_t seg_cap = 0;         // entries per lane segment (a power of two >= kSegMin)
     uint64_t* spill = nullptr;    // 2 * spill_cap: (lane << 32 | vertex) beyond a full segment
     uint32_t* list_v = nullptr;   // list_cap
     uint32_t* list_mrow = nullptr;
@@ -125,6 +131,7 @@ struct Eng {
     uint64_t* stage;
     uint32_t* pend_v;
     uint32_t* seg;
+    uint32_t seg_cap;
     uint64_t* spill;
     uint32_t* list_v;
     uint32_t* list_mrow;
@@ -143,11 +150,12 @@ struct Eng {
     uint64_t m;
     uint64_t pend_cap, list_cap, chunk_cap, spill_cap;
     uint32_t unfused;
-    uint32_t vbits;               // bits of a vertex id in a pair key
     Ctl* ctl;
     uint32_t* starts;             // S
     uint32_t* vcount;             // n
-    uint64_t* pairs;              // pair_cap: (sample index << vbits) | vertex
+    uint32_t* rows_v;             // pair_cap: each finished sample's RR vertices, contiguous, unsorted
+    uint64_t* row_start;          // S: staging position of sample index j's row
+    uint32_t* row_len;            // S: its length
     fbpt_trace_row* trace;        // device copy of the per-level trace (NULL = off)
     uint64_t trace_cap;
     unsigned long long cond;      // cudaGraphConditionalHandle (0 = host-driven loop)
@@ -179,16 +187,20 @@ struct fbpt_graph {
     uint32_t* oeid = nullptr;     // m (edge ids < 2^32)
     fbpt::Workspace* ws = nullptr;
     double rr_hint = 32.0;        // running estimate of RR entries per sample
+    fbpt_tuning tuned = {};       // launch shape measured by fbpt_autotune
+    bool tuned_valid = false;
 };
 
 namespace fbpt {
 int workspace_release(fbpt_graph* g);
+int sample_impl(fbpt_graph* g, uint64_t seed, uint64_t first_id, uint64_t S, const fbpt_opts* opts, fbpt_rrsets* out,
+                fbpt_stats* stats);
+int sample_batched_impl(uint32_t G, fbpt_graph* const* gs, const uint64_t* seeds, const uint64_t* first_ids,
+                        const uint64_t* Ss, const fbpt_opts* opts, fbpt_rrsets* outs, fbpt_stats* stats);
+int autotune_impl(fbpt_graph* g, uint64_t seed, uint64_t S, const fbpt_opts* base, fbpt_tuning* out);
 // Builds g's out-edge CSR if it is not there yet (FBPT_EUNSUPPORTED for m >= 2^32).
 int ensure_out_csr(fbpt_graph* g, cudaStream_t st);
 // Device-wide exclusive scan of n counts into n+1 uint64 offsets (out[n] = total).
 int exclusive_scan_u32(const uint32_t* in, uint64_t* out, uint64_t n, cudaStream_t st);
 int exclusive_scan_u64(const uint64_t* in, uint64_t* out, uint64_t n, cudaStream_t st);
-// Stable LSD radix sort of 64-bit keys on their low `bits` bits; `tmp` holds n keys.
-// The result ends in `keys`.
-int radix_sort_u64(uint64_t* keys, uint64_t* tmp, uint64_t n, uint32_t bits, cudaStream_t st);
 }  // namespace fbpt
