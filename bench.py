@@ -32,7 +32,7 @@ WORKLOAD = "rmat_s22_wc"
 # DRAM bytes (read + write) of one steady-state k_expand launch from the ncu
 # capture summarised in profiles/k_expand_rmat_s22_wc.md; None once the kernel
 # has changed since that capture.
-EXPAND_TRAFFIC_BYTES = 141.18e6
+EXPAND_TRAFFIC_BYTES = None
 METRIC = "RR samples/s (bit-exact RR sets + greedy seeds, R-MAT s22 WC, 1,048,576 samples, k=100)"
 
 
@@ -122,17 +122,64 @@ def run_reference(args):
                       "e2e": {"value": v, "unit": "RR samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
+def bench_batched(fbpt, torch, stream, steps, schedule):
+    """The 32-graph workload (R-MAT scales 12-20, edge factors 8-32, uniform p
+    in [0.01, 0.1], 4,096-262,144 samples per graph): the learned schedule with
+    per-graph autotuned shapes in one batched CUDA-graph launch, against the
+    plain fused form run graph after graph.  Each arm has its own graph
+    handles (and so its own workspaces); each is warmed up once."""
+    w = synth.batched_32()
+    total = sum(w.S)
+    firsts = [0] * len(w.graphs)
+    arms = {}
+    for arm in ("learned_batched", "plain"):
+        dgs = [fbpt.Graph.from_synth(g, stream) for g in w.graphs]
+        t0 = time.perf_counter()
+        if arm == "learned_batched":
+            for dg, seed, S in zip(dgs, w.seeds, w.S):
+                fbpt.autotune(dg, seed, S, schedule=schedule)
+            kw = dict(schedule=schedule)
+        else:
+            kw = dict(launch="host", words=8, slots=1, refill="batch", schedule="push")
+        tune_s = time.perf_counter() - t0
+        outs, _ = fbpt.sample_batched(dgs, w.seeds, firsts, w.S, stream=stream, **kw)
+        del outs
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            outs, st = fbpt.sample_batched(dgs, w.seeds, firsts, w.S, stream=stream, **kw)
+            rr_total = sum(rr.total for rr in outs)
+            del outs
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        arms[arm] = {"value": total / (ms / 1e3), "unit": "RR samples/s", "ms_per_step": ms,
+                     "colour_edge_visits_per_s": st.colour_edge_visits / (ms / 1e3), "rr_entries": rr_total,
+                     "levels": st.levels, "tune_s": tune_s if arm == "learned_batched" else None}
+        for dg in dgs:
+            dg.close()
+    return {"graphs": len(w.graphs), "samples": total, "steps": steps, **arms,
+            "speedup": arms["learned_batched"]["value"] / arms["plain"]["value"]}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--words", type=int, default=8)
+    ap.add_argument("--words", type=int, default=0, help="0 = the autotuned shape")
     ap.add_argument("--slots", type=int, default=0)
+    ap.add_argument("--schedule", default="learned")
     ap.add_argument("--launch", default="graph")
     ap.add_argument("--samples", type=int, default=1 << 20)
+    ap.add_argument("--batched-steps", type=int, default=1,
+                    help="timed steps of the 32-graph batched comparison (0 = skip)")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain-fused comparison on this workload")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffers) measurement")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -155,7 +202,15 @@ def main():
     first = rank * S
     stream = torch.cuda.current_stream()
     dg = fbpt.Graph.from_synth(g, stream)
-    kw = dict(words=args.words, slots=args.slots, launch=args.launch)
+    # launch shape: measured by the autotuner before the timed region (like a
+    # library's algorithm search), unless given on the command line
+    if args.words:
+        kw = dict(words=args.words, slots=args.slots, schedule=args.schedule, launch=args.launch)
+        tuned = None
+    else:
+        tuned = fbpt.autotune(dg, seed, S, schedule=args.schedule)
+        kw = dict(words=tuned["words"], slots=tuned["slots"], blocks=tuned["blocks"], refill="lane",
+                  schedule=tuned["schedule"], launch=args.launch)
 
     def step():
         rr = fbpt.sample(dg, seed, first, S, **kw)
@@ -191,6 +246,37 @@ def main():
     value = S * world * args.steps / (ms / 1e3)
 
     st = stats[-1]
+
+    # ---- the plain fused form on the same workload: Listing 1 with 512
+    # colours per batch, a new batch only when every colour has finished,
+    # push levels only, one host-driven launch per level ----
+    plain_kw = dict(words=8, slots=1, refill="batch", schedule="push", launch="host")
+    plain = None
+    if rank == 0 and world == 1 and not args.no_plain:
+        def plain_step():
+            rr = fbpt.sample(dg, seed, first, S, **plain_kw)
+            fbpt.select_seeds(rr, k)
+            return rr
+        warm = plain_step()
+        del warm
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        psteps = max(1, min(args.steps, 3))
+        e0.record(stream)
+        for _ in range(psteps):
+            prr = plain_step()
+            del prr
+        e1.record(stream)
+        torch.cuda.synchronize()
+        pms = e0.elapsed_time(e1) / psteps
+        plain = {"value": S / (pms / 1e3), "unit": "RR samples/s", "ms_per_step": pms, "steps": psteps,
+                 "shape": plain_kw, "speedup": (S / (ms_step / 1e3)) / (S / (pms / 1e3))}
+
+    batched = None
+    if rank == 0 and world == 1 and args.batched_steps > 0:
+        batched = bench_batched(fbpt, torch, stream, args.batched_steps, args.schedule)
+
     # ---- roofline of the dominant kernel (expand), per launch ----
     # The expand is bound by integer ALU (the Philox rounds).  Algorithmic work:
     # 98 int32 ops per Philox4x32-10 call (10 rounds x (2 mul-hi + 2 mul-lo +
@@ -214,48 +300,53 @@ def main():
             "philox_calls_per_s": st.philox_calls / exp_s if exp_s else 0.0}
 
     # ---- end to end through the C ABI with host buffers ----
-    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
-    h_rp, h_col, h_thr = pin(g.row_ptr.view(np.int64)), pin(g.col.view(np.int32)), pin(g.thr.view(np.int32))
-    e2e_steps = max(1, min(args.steps, 3))
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    h2d = d2h = 0
-    for _ in range(e2e_steps):
-        hg = fbpt.Graph(g.n, h_rp.numpy().view(np.uint64), h_col.numpy().view(np.uint32),
-                        h_thr.numpy().view(np.uint32), stream)
-        rr = fbpt.sample(hg, seed, first, S, **kw)
-        seeds, gains = fbpt.select_seeds(rr, k)
-        off = torch.empty(S + 1, dtype=torch.int64, pin_memory=True)
-        verts = torch.empty(max(rr.total, 1), dtype=torch.int32, pin_memory=True)
-        fbpt.lib().fbpt_rrsets_copy_to_host(fbpt.ctypes.byref(rr.c), off.data_ptr(), verts.data_ptr(), None, None)
-        h2d = g.row_ptr.nbytes + g.col.nbytes + g.thr.nbytes
-        d2h = off.numel() * 8 + rr.total * 4 + k * 12
-        del rr
-        hg.close()
-    torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": S * world / e2e_s, "unit": "RR samples/s", "h2d_bytes_per_step": h2d,
-           "d2h_bytes_per_step": d2h}
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        h_rp, h_col, h_thr = pin(g.row_ptr.view(np.int64)), pin(g.col.view(np.int32)), pin(g.thr.view(np.int32))
+        e2e_steps = max(1, min(args.steps, 3))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h2d = d2h = 0
+        for _ in range(e2e_steps):
+            hg = fbpt.Graph(g.n, h_rp.numpy().view(np.uint64), h_col.numpy().view(np.uint32),
+                            h_thr.numpy().view(np.uint32), stream)
+            rr = fbpt.sample(hg, seed, first, S, **kw)
+            seeds, gains = fbpt.select_seeds(rr, k)
+            off = torch.empty(S + 1, dtype=torch.int64, pin_memory=True)
+            verts = torch.empty(max(rr.total, 1), dtype=torch.int32, pin_memory=True)
+            fbpt.lib().fbpt_rrsets_copy_to_host(fbpt.ctypes.byref(rr.c), off.data_ptr(), verts.data_ptr(), None, None)
+            h2d = g.row_ptr.nbytes + g.col.nbytes + g.thr.nbytes
+            d2h = off.numel() * 8 + rr.total * 4 + k * 12
+            del rr
+            hg.close()
+        torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t0) / e2e_steps
+        if dist:
+            t = torch.tensor([e2e_s], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": S * world / e2e_s, "unit": "RR samples/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(g, seed, 8192)
 
-    # kernels per step: 5 per level, the final sweep, the row-length scan (3), the
+    # kernels per step: 5 or 6 per level, the final sweep, the row-length scan (3), the
     # three row-ordering kernels, greedy 2 per pick + 3
-    launches_step = 5 * int(st.levels) + 1 + 3 + 3 + 2 * k + 3
+    per_level = 5 + (1 if kw.get("schedule", "push") != "push" else 0)  # + the filtered/pull expand
+    launches_step = per_level * int(st.levels) + 1 + 3 + 3 + 2 * k + 3
     if rank == 0:
         print(json.dumps({
             "metric": METRIC, "value": value, "unit": "RR samples/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "graph": g.name, "n": g.n, "m": g.m, "samples_per_gpu": S, "k": k,
-                       "words": args.words, "slots": args.slots, "launch": args.launch,
+                       "shape": kw, "autotuned": tuned,
                        "l2": "inputs larger than L2 (in-CSR + thresholds %.0f MB)" % ((g.m * 8 + g.n * 8) / 1e6)},
+            "plain_fused": plain, "batched_32": batched,
             "colour_edge_visits_per_s": st.colour_edge_visits * world / (ms_step / 1e3),
             "stats": st.as_dict(),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,

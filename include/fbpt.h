@@ -197,7 +197,7 @@ int fbpt_sample(fbpt_graph* g, uint64_t seed, uint64_t first_id, uint64_t S, con
  * GPU runs them concurrently, and tasks that share a graph (and so its
  * workspace) are chained.  The whole batch is ONE cudaGraphLaunch.  When
  * opts->words == 0, each graph runs with the shape fbpt_autotune stored on it
- * (words, slots, refill, blocks), else the fixed default.  Tasks whose RR sets
+ * (words, slots, refill, blocks and schedule), else the fixed default.  Tasks whose RR sets
  * outgrew their buffers run again on their own.  Traces are not recorded.  On
  * error every outs[i] is released. */
 int fbpt_sample_batched(uint32_t G, fbpt_graph* const* gs, const uint64_t* seeds, const uint64_t* first_ids,
@@ -210,18 +210,22 @@ int fbpt_sample_batched(uint32_t G, fbpt_graph* const* gs, const uint64_t* seeds
 typedef struct fbpt_tuning {
     uint32_t words, slots, refill, blocks;
     uint32_t candidates;      /* shapes measured */
-    uint32_t reserved;
+    uint32_t schedule;        /* enum fbpt_schedule kept for this graph */
     uint64_t probe_samples;   /* samples per timed probe */
     double probe_rate;        /* samples per second of the chosen shape in its probe */
     double rr_per_sample;     /* mean RR set size seen by the probes */
 } fbpt_tuning;
 
-/* Times sampling runs of g (sample ids 0 .. min(S, 8192) - 1 under seed; each
- * shape is warmed up on a smaller probe first) for row widths 1, 2, 4, ..., 64
- * words (at most one lane per probe sample), then for the best width with
- * 1, 1/2, 1/4 and 1/8 of the resident CTAs, and keeps the fastest width and the
- * fewest CTAs within 3% of its rate.  base supplies the schedule and policy
- * (NULL = push).  The result is stored on g (used by fbpt_sample_batched) and
+/* Times sampling runs of g on sample ids 0 .. P - 1 under seed, where P (in
+ * [min(S, 4096), min(S, 65536)]) makes one probe take about 50 ms, measured on
+ * a first run of min(S, 4096) samples.  Each shape is warmed up on P / 8
+ * samples first.  Row widths 1, 2, 4, ..., 64 words (at most one lane per probe
+ * sample), then the best width with 1, 1/2, 1/4 and 1/8 of the resident CTAs:
+ * it keeps the fastest width and the fewest CTAs within 3% of its rate.  base supplies the schedule and policy
+ * (NULL = push); when base->words is set, base->words * base->slots (slots 0
+ * read as 1) caps the widths tried.  A learned (or heuristic) schedule is then
+ * judged at that shape against the heuristic (or learned, with a policy) and
+ * plain push: another schedule is kept only if it is at least 3% faster.  The result is stored on g (used by fbpt_sample_batched) and
  * copied to out (may be NULL).  Output bits never depend on the shape. */
 int fbpt_autotune(fbpt_graph* g, uint64_t seed, uint64_t S, const fbpt_opts* base, fbpt_tuning* out);
 /* The shape stored on g by fbpt_autotune; FBPT_EINVAL if it was never tuned. */

@@ -40,12 +40,14 @@ class Opts(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("words", ctypes.c_uint32), ("slots", ctypes.c_uint32), ("refill", ctypes.c_uint32),
-                ("blocks", ctypes.c_uint32), ("candidates", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("blocks", ctypes.c_uint32), ("candidates", ctypes.c_uint32), ("schedule", ctypes.c_uint32),
                 ("probe_samples", ctypes.c_uint64), ("probe_rate", ctypes.c_double),
                 ("rr_per_sample", ctypes.c_double)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["schedule"] = {v: k for k, v in SCHED.items()}.get(d["schedule"], d["schedule"])
+        return d
 
 
 class RRSetsC(ctypes.Structure):
@@ -230,6 +232,16 @@ class RRSets:
         _check(lib().fbpt_rrsets_copy_to_host(ctypes.byref(self.c), off.ctypes.data, verts.ctypes.data,
                                               starts.ctypes.data, vcount.ctypes.data))
         return off, verts[:total], starts, vcount
+
+    def index_to_host(self):
+        """(offsets[S+1], starts[S], vcount[n]) without the vertex array."""
+        S, n = self.S, int(self.c.n)
+        off = np.empty(S + 1, np.uint64)
+        starts = np.empty(S, np.uint32)
+        vcount = np.empty(n, np.uint32)
+        _check(lib().fbpt_rrsets_copy_to_host(ctypes.byref(self.c), off.ctypes.data, None, starts.ctypes.data,
+                                              vcount.ctypes.data))
+        return off, starts, vcount
 
     def rows(self, first, count):
         """Host copy of rows first .. first+count-1 only (fbpt_rrsets_copy_rows):

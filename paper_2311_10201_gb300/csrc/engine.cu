@@ -71,14 +71,23 @@ struct CommitWarp {
     uint32_t es[32];                // its first entry
 };
 
+struct SchedHead {
+    unsigned long long next_j, pair_cursor, new_packed, new_colours, tick, tick_limit;
+    unsigned long long list_count, list_groups, list_colours;
+    unsigned long long ph_t0[3], ph_t1[3];
+    uint32_t err, refill, sched, dir, frontier_lanes, pend_count, spill_cur;
+};
+
 struct Smem {
     uint32_t lane[kMaxLanes + 1];   // expand: sample index per lane; sweep, schedule: entry prefixes
     uint32_t act[2 * kMaxWords];    // commit: lanes seen in this CTA's new units (32-bit halves)
     CommitWarp cw[kThreads / 32];   // commit
     uint64_t fin[kMaxWords];        // sweep: finished lanes (spill-log sweep)
-    uint32_t cnt[kMaxWords + 1];    // schedule: per-word counts, then their prefix
-    uint32_t tsum[kThreads + 1];    // schedule: per-thread sums of the block scan
-    unsigned long long wsum[kMaxWords];  // schedule: finished lanes' row lengths per word, then bases
+    // schedule: the control fields it reads (loaded in parallel), lane masks
+    // per word, block-scan scratch
+    SchedHead h;
+    unsigned long long still[kMaxWords], sfin[kMaxWords], init[kMaxWords];
+    unsigned long long bscan[kThreads / 32 + 1];
     float feat[8], h1[kPolicyHidden], h2[kPolicyHidden], out[kPolicyOut];
     uint32_t last, abort, nstill, dir;
 };
@@ -233,8 +242,9 @@ __device__ __forceinline__ bool grp_load(const Eng& E, uint32_t u, uint64_t j, G
     return inrow != 0;
 }
 
-__device__ __forceinline__ void grp_run(const Eng& E, const Smem& sm, const Grp& G, const PhiloxKeys& K,
-                                        bool filtered, uint64_t& n_calls) {
+template <bool filtered>
+__device__ __forceinline__ void grp_run(const Eng& E, const uint32_t* lane_j, const Grp& G, const PhiloxKeys& K,
+                                        uint64_t& n_calls) {
     const bool need = (G.valid & ~G.sure) != 0;  // some edge needs a draw
     const uint32_t qlo = (uint32_t)G.q, qhi = (uint32_t)(G.q >> 32);
     const uint32_t f_lo = (uint32_t)E.first_id, f_hi = (uint32_t)(E.first_id >> 32);
@@ -259,7 +269,7 @@ __device__ __forceinline__ void grp_run(const Eng& E, const Smem& sm, const Grp&
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 uint32_t xx = (uint32_t)(x >> (32 * h));
-                const uint32_t* lj = &sm.lane[(i << 6) + 32 * h];
+                const uint32_t* lj = &lane_j[(i << 6) + 32 * h];
                 uint32_t z0 = 0, z1 = 0, z2 = 0, z3 = 0;
                 while (xx) {
                     const uint32_t c = __ffs(xx) - 1;
@@ -323,7 +333,8 @@ __device__ __forceinline__ uint32_t chunk_unit(const Eng& E, uint32_t c, uint64_
 // push (word e & 3 of Philox(sample, e >> 2)), so the closure is unchanged.  A
 // warp owns w and stops once every missing colour has been found; no draw is
 // spent on a colour w already has.  Needs WB <= kPullMaxWords.
-__device__ void dev_pull(const Eng& E, const Smem& sm, const PhiloxKeys& K, uint64_t& n_edges, uint64_t& n_calls) {
+__device__ __forceinline__ void dev_pull(const Eng& E, const uint32_t* lane_j, const PhiloxKeys& K, uint64_t& n_edges,
+                                      uint64_t& n_calls) {
     Ctl* ctl = E.ctl;
     const uint32_t WB = E.WB;
     const uint32_t tick = (uint32_t)L2(&ctl->tick);
@@ -366,7 +377,7 @@ __device__ void dev_pull(const Eng& E, const Smem& sm, const PhiloxKeys& K, uint
                         while (f) {
                             const uint32_t c = __ffsll((long long)f) - 1;
                             f &= f - 1;
-                            const uint32_t j = sm.lane[(i << 6) + c];
+                            const uint32_t j = lane_j[(i << 6) + c];
                             const uint32_t slo = f_lo + j;
                             const uint32_t shi = f_hi + (slo < j ? 1u : 0u);
                             const uint4 r = philox4x32_10(make_uint4(slo, shi, e >> 2, 0u), K);
@@ -396,25 +407,14 @@ __device__ void dev_pull(const Eng& E, const Smem& sm, const PhiloxKeys& K, uint
 
 // Edge-balanced: the frontier's 4-edge groups form one index space; a warp
 // takes kChunksPerGrab chunks of 32 consecutive groups per atomic, one group
-// per lane, and works on two chunks at a time.
-__device__ void dev_expand(const Eng& E, Smem& sm) {
+// per lane (FBPT_EXPAND_ILP chunks at a time).  One instance per push variant,
+// so that the plain push loop carries no register of the filtered one.
+template <bool filtered>
+__device__ __forceinline__ void expand_push(const Eng& E, const uint32_t* lane_j, const PhiloxKeys& K, uint64_t G,
+                                            uint64_t U, uint64_t nchunks, uint64_t& n_edges, uint64_t& n_calls) {
     Ctl* ctl = E.ctl;
-    const uint64_t G = L2(&ctl->list_groups);
-    if (G == 0) return;
-    const uint64_t U = L2(&ctl->list_count);
-    const uint64_t nchunks = (G + kChunk - 1) / kChunk;
-    if (nchunks > E.chunk_cap || U > E.list_cap) return;  // overflow already flagged by commit
-    phase_begin(ctl, 0);
-    __syncthreads();
-    for (uint32_t l = threadIdx.x; l < 64u * E.WB; l += blockDim.x) sm.lane[l] = L2(&ctl->lane_j[l]);
-    __syncthreads();
     const uint32_t lane = lane_id();
-    const PhiloxKeys K = philox_keys(E.seed);
-    uint64_t n_edges = 0, n_calls = 0;
-    const uint32_t dir = L2(&ctl->dir);
-    const bool filtered = dir == kDirFiltered;
-    if (dir == kDirPull && E.frontd) dev_pull(E, sm, K, n_edges, n_calls);
-    else for (;;) {
+    for (;;) {
         uint32_t c0 = 0;
         if (lane == 0) c0 = atomicAdd(&ctl->chunk_next, kChunksPerGrab);
         c0 = __shfl_sync(0xffffffffu, c0, 0);
@@ -431,10 +431,40 @@ __device__ void dev_expand(const Eng& E, Smem& sm) {
             Grp A, B;
             const bool la = ga < G && grp_load(E, ua, ja, A, n_edges);
             const bool lb = two && gbb < G && grp_load(E, ub, jb, B, n_edges);
-            if (la) grp_run(E, sm, A, K, filtered, n_calls);
-            if (lb) grp_run(E, sm, B, K, filtered, n_calls);
+            if (la) grp_run<filtered>(E, lane_j, A, K, n_calls);
+            if (lb) grp_run<filtered>(E, lane_j, B, K, n_calls);
         }
     }
+}
+
+// The expand phase.  part selects which directions this instance runs (the
+// per-level kernels split them so that the plain push kernel carries no
+// register of the others): kPartPush, kPartAlt (filtered push and pull) or
+// kPartAll (the persistent kernel).
+enum ExpandPart : int { kPartPush = 0, kPartAlt = 1, kPartAll = 2 };
+
+template <int part>
+__device__ void dev_expand(const Eng& E, uint32_t* lane_j) {
+    Ctl* ctl = E.ctl;
+    const uint64_t G = L2(&ctl->list_groups);
+    const uint32_t dir = L2(&ctl->dir);
+    const bool pull = dir == kDirPull && E.frontd;
+    if (part == kPartPush && dir != kDirPush) return;
+    if (part == kPartAlt && dir == kDirPush) return;
+    if (G == 0) return;
+    const uint64_t U = L2(&ctl->list_count);
+    const uint64_t nchunks = (G + kChunk - 1) / kChunk;
+    if (nchunks > E.chunk_cap || U > E.list_cap) return;  // overflow already flagged by commit
+    phase_begin(ctl, 0);
+    __syncthreads();
+    for (uint32_t l = threadIdx.x; l < 64u * E.WB; l += blockDim.x) lane_j[l] = L2(&ctl->lane_j[l]);
+    __syncthreads();
+    const uint32_t lane = lane_id();
+    const PhiloxKeys K = philox_keys(E.seed);
+    uint64_t n_edges = 0, n_calls = 0;
+    if (part != kPartPush && pull) dev_pull(E, lane_j, K, n_edges, n_calls);
+    else if (part != kPartPush && dir == kDirFiltered) expand_push<true>(E, lane_j, K, G, U, nchunks, n_edges, n_calls);
+    else if (part != kPartAlt) expand_push<false>(E, lane_j, K, G, U, nchunks, n_edges, n_calls);
     n_edges = warp_sum(n_edges);
     n_calls = warp_sum(n_calls);
     if (lane == 0) {
@@ -570,6 +600,7 @@ __device__ void dev_commit(const Eng& E, Smem& sm) {
                 pos = __shfl_sync(0xffffffffu, pos, leader) + __popc(peers & lanemask_lt());
                 const bool spill = ok && pos >= E.seg_cap;
                 if (ok && !spill) E.seg[(uint64_t)l * E.seg_cap + pos] = v;
+                if (!__any_sync(0xffffffffu, spill)) continue;
                 const uint64_t sp = warp_alloc<unsigned long long>(&ctl->spill_len[spill_cur], spill ? 1ull : 0ull);
                 if (spill) {
                     if (sp < E.spill_cap)
@@ -714,72 +745,93 @@ __device__ void policy_forward(const float* P, Smem& sm) {
     __syncthreads();
 }
 
-// ---- schedule (one CTA, at least kMaxWords threads) ------------------------------------
+// ---- schedule (one CTA of kThreads threads) ---------------------------------------------
+
+// Exclusive prefix over the CTA's threads (all must call); total gets the sum.
+__device__ __forceinline__ unsigned long long block_excl_scan(unsigned long long v, unsigned long long* scratch,
+                                                              unsigned long long& total) {
+    const uint32_t lane = lane_id(), warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const unsigned long long incl = warp_incl_scan(v);
+    if (lane == 31) scratch[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const unsigned long long x = lane < nw ? scratch[lane] : 0ull;
+        const unsigned long long xi = warp_incl_scan(x);
+        if (lane < nw) scratch[lane] = xi - x;
+        if (lane == nw - 1) scratch[kThreads / 32] = xi;
+    }
+    __syncthreads();
+    total = scratch[kThreads / 32];
+    const unsigned long long r = scratch[warp] + incl - v;
+    __syncthreads();
+    return r;
+}
 
 // Lanes that held a sample but are absent from the new frontier have finished
 // (the next sweep emits them).  Free lanes take the next sample ids, right away
 // (lane refill) or once no lane is still traversing (batch mode).  The new
 // frontier list becomes the expand's input; the loop continues while any
-// lane holds a sample.
+// lane holds a sample.  Every thread owns a run of consecutive lanes (inside
+// one word), so lane-order prefixes are block scans.
 __device__ void dev_schedule(const Eng& E, Smem& sm) {
     Ctl* ctl = E.ctl;
-    const uint32_t i = threadIdx.x;
-    const bool mine = i < E.WB;
-    const uint32_t err = L2(&ctl->error);
-    uint64_t still = 0, fin = 0;
-    if (mine) {
-        const uint64_t run = L2(&ctl->run_w[i]);
-        const uint64_t act = L2(&ctl->act_w[i]);
-        still = run & act;
-        fin = run & ~act;
-        sm.cnt[i] = __popcll(fin);
+    const uint32_t t = threadIdx.x;
+    const uint32_t WB = E.WB, L = 64u * WB;
+    SchedHead& h = sm.h;
+    // 1. the control fields this step reads, one load per thread
+    switch (t) {
+        case 0: h.err = L2(&ctl->error); break;
+        case 1: h.next_j = L2(&ctl->next_j); break;
+        case 2: h.pair_cursor = L2(&ctl->pair_cursor); break;
+        case 3: h.refill = L2(&ctl->refill); break;
+        case 4: h.new_packed = L2(&ctl->new_packed); break;
+        case 5: h.new_colours = L2(&ctl->new_colours); break;
+        case 6: h.sched = L2(&ctl->sched); break;
+        case 7: h.tick = L2(&ctl->tick); break;
+        case 8: h.list_groups = L2(&ctl->list_groups); break;
+        case 9: h.list_count = L2(&ctl->list_count); break;
+        case 10: h.list_colours = L2(&ctl->list_colours); break;
+        case 11: h.pend_count = L2(&ctl->pend_count); break;
+        case 12: h.dir = L2(&ctl->dir); break;
+        case 13: h.frontier_lanes = L2(&ctl->frontier_lanes); break;
+        case 14: h.spill_cur = L2(&ctl->spill_cur); break;
+        case 15: h.tick_limit = L2(&ctl->tick_limit); break;
+        case 16: case 17: case 18: h.ph_t0[t - 16] = L2(&ctl->ph_t0[t - 16]); break;
+        case 19: case 20: case 21: h.ph_t1[t - 19] = L2(&ctl->ph_t1[t - 19]); break;
+        default: break;
     }
-    if (mine) sm.tsum[i] = __popcll(still);
-    const bool any_still = __syncthreads_or(still != 0);
-    // finished lanes, word by word: base index of each word's finished lanes
-    if (threadIdx.x == 0) {
-        uint32_t acc = 0, ns = 0;
-        for (uint32_t w = 0; w < E.WB; ++w) {
-            const uint32_t c = sm.cnt[w];
-            sm.cnt[w] = acc;
-            acc += c;
-            ns += sm.tsum[w];
-        }
-        sm.cnt[E.WB] = acc;
-        sm.nstill = ns;
-    }
-    __syncthreads();
-    // staging ranges of the finished samples' rows, word by word in lane order
-    if (mine) {
-        uint64_t t = 0, f = fin;
-        while (f) {
-            const uint32_t c = __ffsll((long long)f) - 1;
-            f &= f - 1;
-            t += L2(&ctl->lane_cnt[(i << 6) + c]);
-        }
-        sm.wsum[i] = t;
+    if (t < WB) {
+        const unsigned long long run = L2(&ctl->run_w[t]), act = L2(&ctl->act_w[t]);
+        sm.still[t] = run & act;
+        sm.sfin[t] = run & ~act;
+        sm.init[t] = 0;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned long long acc = L2(&ctl->pair_cursor);
-        for (uint32_t w = 0; w < E.WB; ++w) {
-            const unsigned long long t = sm.wsum[w];
-            sm.wsum[w] = acc;
-            acc += t;
-        }
-        ctl->pair_cursor = acc;
-    }
-    __syncthreads();
-    const uint32_t F = sm.cnt[E.WB];
+    // lanes per thread: the smallest power of two with per * blockDim >= L,
+    // so that a run never straddles two words (per <= 16 for L <= 4096)
+    uint32_t per = 1;
+    while (per * blockDim.x < L) per <<= 1;
+    const uint32_t a0 = min(t * per, L), a1 = min(a0 + per, L);
+    const uint32_t wi = a0 >> 6;
+    const unsigned long long runmask = per >= 64 ? ~0ull : ((1ull << per) - 1ull);
+    const unsigned long long myfin = a0 < a1 ? (sm.sfin[wi] >> (a0 & 63)) & runmask : 0ull;
+    const unsigned long long mystill = a0 < a1 ? (sm.still[wi] >> (a0 & 63)) & runmask : 0ull;
+    // 2. finished lanes: their count and row lengths in lane order
+    unsigned long long rsum = 0;
+    for (unsigned long long f = myfin; f; f &= f - 1)
+        rsum += L2(&ctl->lane_cnt[a0 + __ffsll((long long)f) - 1]);
+    unsigned long long F64 = 0, R64 = 0, S64 = 0, N64 = 0, ST64 = 0;
+    const unsigned long long k0 = block_excl_scan((unsigned long long)__popcll(myfin), sm.bscan, F64);
+    const unsigned long long rb0 = block_excl_scan(rsum, sm.bscan, R64);
+    const uint32_t F = (uint32_t)F64;
+    // 3. each finished lane's row: staging range, sample index, entry of the fin list
     bool spilled = false;
-    if (mine) {
-        uint32_t k = sm.cnt[i];
-        uint64_t f = fin;
-        unsigned long long rb = sm.wsum[i];
-        while (f) {
-            const uint32_t c = __ffsll((long long)f) - 1;
-            f &= f - 1;
-            const uint32_t l = (i << 6) + c;
+    unsigned long long segsum = 0;
+    {
+        unsigned long long rb = h.pair_cursor + rb0;
+        uint32_t k = (uint32_t)k0;
+        for (unsigned long long f = myfin; f; f &= f - 1) {
+            const uint32_t l = a0 + __ffsll((long long)f) - 1;
             const uint32_t rc = L2(&ctl->lane_cnt[l]);
             const uint32_t j = L2(&ctl->lane_j[l]);
             ctl->retired_j[l] = j;
@@ -789,88 +841,56 @@ __device__ void dev_schedule(const Eng& E, Smem& sm) {
             rb += rc;
             ctl->lane_cnt[l] = 0;
             ctl->fin_lane[k] = l;
-            sm.lane[k] = min(rc, E.seg_cap);
+            const uint32_t sg = min(rc, E.seg_cap);
+            sm.lane[k] = sg;
+            segsum += sg;
             spilled |= rc > E.seg_cap;
             ++k;
         }
-        ctl->fin_mask[i] = fin;
+    }
+    // exclusive prefix of the finished lanes' segment entry counts (sweep input)
+    {
+        unsigned long long run = block_excl_scan(segsum, sm.bscan, S64);
+        for (uint32_t k = (uint32_t)k0; k < (uint32_t)k0 + (uint32_t)__popcll(myfin); ++k) {
+            ctl->fin_pre[k] = (uint32_t)run;
+            run += sm.lane[k];
+        }
     }
     const bool any_spill = __syncthreads_or(spilled);
-    // exclusive prefix of the finished lanes' segment entry counts
+    if (t < WB) ctl->fin_mask[t] = sm.sfin[t];
+    // 4. refill: lanes without a sample take the next ids in lane order
+    const bool any_still = __syncthreads_or(mystill != 0);
+    const bool may_refill = h.err == 0 && (h.refill == kRefillLane || !any_still);
+    const unsigned long long need = may_refill ? (~mystill & (a0 < a1 ? runmask : 0ull)) : 0ull;
+    const unsigned long long r0 = block_excl_scan((unsigned long long)__popcll(need), sm.bscan, N64);
+    const unsigned long long avail = E.S > h.next_j ? E.S - h.next_j : 0ull;
     {
-        const uint32_t per = (F + blockDim.x - 1) / blockDim.x;
-        const uint32_t a0 = min(threadIdx.x * per, F), a1 = min(a0 + per, F);
-        uint32_t t = 0;
-        for (uint32_t k = a0; k < a1; ++k) t += sm.lane[k];
-        sm.tsum[threadIdx.x] = t;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            uint32_t acc = 0;
-            for (uint32_t q = 0; q < blockDim.x; ++q) {
-                const uint32_t x = sm.tsum[q];
-                sm.tsum[q] = acc;
-                acc += x;
-            }
-            sm.tsum[blockDim.x] = acc;
-        }
-        __syncthreads();
-        uint32_t run = sm.tsum[threadIdx.x];
-        for (uint32_t k = a0; k < a1; ++k) {
-            const uint32_t x = sm.lane[k];
-            ctl->fin_pre[k] = run;
-            run += x;
-        }
-        if (threadIdx.x == 0) {
-            ctl->fin_pre[F] = sm.tsum[blockDim.x];
-            ctl->fin_count = F;
-        }
-    }
-    __syncthreads();
-    const bool may_refill = err == 0 && (L2(&ctl->refill) == kRefillLane || !any_still);
-    uint64_t need = 0;
-    if (mine) {
-        need = may_refill ? ~still : 0ull;
-        sm.cnt[i] = __popcll(need);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        uint32_t acc = 0;
-        for (uint32_t w = 0; w < E.WB; ++w) {
-            const uint32_t c = sm.cnt[w];
-            sm.cnt[w] = acc;
-            acc += c;
-        }
-        sm.cnt[E.WB] = acc;
-    }
-    __syncthreads();
-    const uint64_t base_j = L2(&ctl->next_j);
-    const uint64_t avail = E.S > base_j ? E.S - base_j : 0;
-    uint64_t init = 0;
-    if (mine) {
-        uint64_t r = sm.cnt[i];
-        uint64_t nd = need;
-        while (nd && r < avail) {
+        unsigned long long r = r0, got = 0;
+        for (unsigned long long nd = need; nd && r < avail; nd &= nd - 1, ++r) {
             const uint32_t c = __ffsll((long long)nd) - 1;
-            nd &= nd - 1;
-            ctl->lane_j[(i << 6) + c] = (uint32_t)(base_j + r);
-            init |= 1ull << c;
-            ++r;
+            ctl->lane_j[a0 + c] = (uint32_t)(h.next_j + r);
+            got |= 1ull << c;
         }
-        ctl->init_w[i] = init;
-        ctl->run_w[i] = still | init;
-        ctl->still_w[i] = still;
-        ctl->act_w[i] = 0;
+        if (got) atomicOr(&sm.init[wi], got << (a0 & 63));
     }
-    const bool any_run = __syncthreads_or((still | init) != 0);
-    // direction of the coming level
+    block_excl_scan((unsigned long long)__popcll(mystill), sm.bscan, ST64);  // lanes still traversing
+    if (t < WB) {
+        ctl->init_w[t] = sm.init[t];
+        ctl->run_w[t] = sm.still[t] | sm.init[t];
+        ctl->still_w[t] = sm.still[t];
+        ctl->act_w[t] = 0;
+    }
+    const bool any_run = __syncthreads_or(t < WB && (sm.still[t] | sm.init[t]) != 0);
+    const uint32_t nstill = (uint32_t)ST64;
+    // 5. direction of the coming level
     {
-        const unsigned long long np = L2(&ctl->new_packed);
+        const unsigned long long np = h.new_packed;
         const double U = (double)(np & kUnitMask), G = (double)(np >> kUnitBits);
-        const double C = (double)L2(&ctl->new_colours);
-        const uint32_t sched = L2(&ctl->sched);
+        const double C = (double)h.new_colours;
+        const uint32_t sched = h.sched;
         const bool pull_ok = E.frontd != nullptr;
-        if (threadIdx.x == 0) {
-            level_features(sm.feat, U, G, C, (double)sm.nstill, (double)E.m);
+        if (t == 0) {
+            level_features(sm.feat, U, G, C, (double)nstill, (double)E.m);
             uint32_t d = kDirPush;
             if (sched == FBPT_SCHED_PULL && pull_ok) d = kDirPull;
             else if (sched == FBPT_SCHED_FILTERED) d = kDirFiltered;
@@ -881,7 +901,7 @@ __device__ void dev_schedule(const Eng& E, Smem& sm) {
         __syncthreads();
         if (sched == FBPT_SCHED_LEARNED && E.policy) {
             policy_forward(E.policy, sm);
-            if (threadIdx.x == 0) {
+            if (t == 0) {
                 uint32_t best = kDirPush;
                 if (sm.out[kDirFiltered] < sm.out[best]) best = kDirFiltered;
                 if (pull_ok && sm.out[kDirPull] < sm.out[best]) best = kDirPull;
@@ -890,52 +910,50 @@ __device__ void dev_schedule(const Eng& E, Smem& sm) {
             __syncthreads();
         }
     }
-    if (threadIdx.x == 0) {
+    // 6. the level's bookkeeping (one thread, from the loaded fields)
+    if (t == 0) {
+        const uint32_t err = h.err;
+        ctl->pair_cursor = h.pair_cursor + R64;
+        ctl->fin_pre[F] = (uint32_t)S64;
+        ctl->fin_count = F;
         // a lane whose segment overflowed has entries in the spill log: the next
         // sweep reads the log and writes the surviving entries to the other buffer
         if (any_spill) {
-            const uint32_t dst = L2(&ctl->spill_cur) ^ 1u;
+            const uint32_t dst = h.spill_cur ^ 1u;
             ctl->spill_cur = dst;
             ctl->spill_len[dst] = 0;
         }
         ctl->spill_sweep = any_spill ? 1u : 0u;
-        const uint64_t assigned = min((uint64_t)sm.cnt[E.WB], avail);
-        const unsigned long long tick = L2(&ctl->tick);
-        const unsigned long long done_groups = L2(&ctl->list_groups);  // the level just expanded
+        const unsigned long long assigned = N64 < avail ? N64 : avail;
+        const unsigned long long tick = h.tick;
         if (E.trace && tick < E.trace_cap) {
             fbpt_trace_row& row = E.trace[tick];
             row.level = tick;
-            row.units = L2(&ctl->list_count);
-            row.groups = L2(&ctl->list_groups);
-            row.colours = L2(&ctl->list_colours);
-            row.pending = L2(&ctl->pend_count);
-            row.active_lanes = sm.nstill;
+            row.units = h.list_count;
+            row.groups = h.list_groups;
+            row.colours = h.list_colours;
+            row.pending = h.pend_count;
+            row.active_lanes = nstill;
             row.finished_lanes = F;
             row.started_lanes = assigned;
             uint64_t* pt[3] = {&row.expand_ns, &row.commit_ns, &row.sweep_ns};
-            for (int p = 0; p < 3; ++p) {
-                const unsigned long long t0 = L2(&ctl->ph_t0[p]), t1 = L2(&ctl->ph_t1[p]);
-                *pt[p] = t1 > t0 ? t1 - t0 : 0;
-            }
-            row.direction = L2(&ctl->dir);
-            row.frontier_lanes = L2(&ctl->frontier_lanes);
+            for (int p = 0; p < 3; ++p) *pt[p] = h.ph_t1[p] > h.ph_t0[p] ? h.ph_t1[p] - h.ph_t0[p] : 0;
+            row.direction = h.dir;
+            row.frontier_lanes = h.frontier_lanes;
         }
-        ctl->list_colours = err ? 0 : L2(&ctl->new_colours);
+        ctl->list_colours = err ? 0 : h.new_colours;
         ctl->new_colours = 0;
-        ctl->next_j = base_j + assigned;
-        ctl->st_assigned += assigned;
-        const unsigned long long np = L2(&ctl->new_packed);
+        ctl->next_j = h.next_j + assigned;
+        atomicAdd(&ctl->st_assigned, assigned);
+        const unsigned long long np = h.new_packed;
         ctl->list_count = err ? 0 : (np & kUnitMask);
         ctl->list_groups = err ? 0 : (np >> kUnitBits);
-        ctl->st_units += np & kUnitMask;
-        if (done_groups != 0) {
-            if (L2(&ctl->dir) == kDirPull) ctl->st_pull += 1; else ctl->st_push += 1;
-        }
+        atomicAdd(&ctl->st_units, np & kUnitMask);
+        if (h.list_groups != 0) atomicAdd(h.dir == kDirPull ? &ctl->st_pull : &ctl->st_push, 1ull);
         ctl->dir = sm.dir;
-        ctl->frontier_lanes = sm.nstill;
+        ctl->frontier_lanes = nstill;
         for (int p = 0; p < 3; ++p) {
-            const unsigned long long t0 = L2(&ctl->ph_t0[p]), t1 = L2(&ctl->ph_t1[p]);
-            if (t1 > t0) ctl->st_phase_ns[p] += t1 - t0;
+            if (h.ph_t1[p] > h.ph_t0[p]) atomicAdd(&ctl->st_phase_ns[p], h.ph_t1[p] - h.ph_t0[p]);
             ctl->ph_t0[p] = ~0ull;
             ctl->ph_t1[p] = 0;
         }
@@ -944,7 +962,7 @@ __device__ void dev_schedule(const Eng& E, Smem& sm) {
         ctl->pend_count = 0;
         ctl->tick = tick + 1;
         uint32_t run = any_run ? 1u : 0u;
-        if (tick + 1 > L2(&ctl->tick_limit)) {
+        if (tick + 1 > h.tick_limit) {
             atomicOr(&ctl->error, (unsigned)kErrTickLimit);
             run = 0;
         }
@@ -964,8 +982,12 @@ __global__ void __launch_bounds__(kThreads) k_sweep(const Eng E) {
 }
 __global__ void __launch_bounds__(kThreads) k_init(const Eng E) { dev_init(E); }
 __global__ void __launch_bounds__(kThreads, FBPT_EXPAND_MINB) k_expand(const Eng E) {
-    __shared__ Smem sm;
-    dev_expand(E, sm);
+    __shared__ uint32_t lane_j[kMaxLanes];
+    dev_expand<kPartPush>(E, lane_j);
+}
+__global__ void __launch_bounds__(kThreads) k_expand_alt(const Eng E) {
+    __shared__ uint32_t lane_j[kMaxLanes];
+    dev_expand<kPartAlt>(E, lane_j);
 }
 __global__ void __launch_bounds__(kThreads) k_commit(const Eng E) {
     __shared__ Smem sm;
@@ -1029,7 +1051,7 @@ __global__ void __launch_bounds__(kThreads) k_run(const Eng E) {
     for (;;) {
         dev_sweep(E, sm);  // lanes finished at the previous level
         dev_init(E);       // lanes given a sample at the previous level
-        dev_expand(E, sm);
+        dev_expand<kPartAll>(E, sm.lane);
         if (!grid_barrier(E, sm, gen, false)) return;
         dev_commit(E, sm);
         if (!grid_barrier(E, sm, gen, true)) return;
@@ -1207,6 +1229,7 @@ int launch_level(const Eng& E, cudaStream_t st, int blocks) {
     k_sweep<<<blocks, kThreads, 0, st>>>(E);
     k_init<<<std::min(blocks, (int)(64 * E.WB + kThreads - 1) / kThreads), kThreads, 0, st>>>(E);
     k_expand<<<blocks, kThreads, 0, st>>>(E);
+    if (E.alt) k_expand_alt<<<blocks, kThreads, 0, st>>>(E);
     k_commit<<<blocks, kThreads, 0, st>>>(E);
     k_schedule<<<1, kThreads, 0, st>>>(E);
     FBPT_CUDA_TRY(cudaGetLastError());
@@ -1548,6 +1571,7 @@ int run_arm(Run& r) {
     E.orow = g->orow; E.odst = g->odst; E.oeid = g->oeid;
     E.frontd = ws->frontd; E.fstamp = ws->fstamp;
     E.policy = (r.o.schedule == FBPT_SCHED_LEARNED && r.o.policy) ? r.o.policy->d_params : nullptr;
+    E.alt = r.o.schedule == FBPT_SCHED_PUSH ? 0u : 1u;
     E.m = g->m;
     E.pend_cap = ws->pend_cap; E.list_cap = ws->list_cap; E.chunk_cap = ws->chunk_cap;
     E.spill_cap = ws->spill_cap;
@@ -1793,6 +1817,7 @@ int sample_batched_impl(uint32_t G, fbpt_graph* const* gs, const uint64_t* seeds
             oi[i].slots = gs[i]->tuned.slots;
             oi[i].refill = gs[i]->tuned.refill;
             oi[i].blocks = gs[i]->tuned.blocks;
+            oi[i].schedule = gs[i]->tuned.schedule;
         }
     }
     if (base.launch == FBPT_LAUNCH_HOST) {
@@ -1898,15 +1923,38 @@ int autotune_impl(fbpt_graph* g, uint64_t seed, uint64_t S, const fbpt_opts* bas
     o.trace_cap = 0;
     o.unfused = 0;
     if (o.launch == FBPT_LAUNCH_PERSISTENT) o.launch = FBPT_LAUNCH_GRAPH;
-    const uint64_t P = std::min<uint64_t>(S, 8192);
+    // probe size: about kProbeMs of sampling per probe, measured on a first
+    // run of 4,096 samples, within [4,096, 65,536] samples (and at most S)
+    constexpr double kProbeMs = 50.0;
+    const uint64_t P0 = std::min<uint64_t>(S, 4096);
+    uint64_t P = P0;
+    {
+        fbpt_opts q = o;
+        q.words = 8;
+        q.slots = 1;
+        q.refill = FBPT_REFILL_LANE;
+        q.blocks = 0;
+        if (q.schedule == FBPT_SCHED_PULL) q.schedule = FBPT_SCHED_HEURISTIC;
+        fbpt_rrsets rr;
+        fbpt_stats s0 = {};
+        for (int rep = 0; rep < 2; ++rep) {
+            s0 = fbpt_stats{};
+            FBPT_TRY(sample_impl(g, seed, 0, P0, &q, &rr, &s0));
+            release_out(&rr);
+        }
+        if (s0.ms_total > 0)
+            P = std::max<uint64_t>(P0, std::min<uint64_t>(std::min<uint64_t>(S, 65536),
+                                                          (uint64_t)((double)P0 * kProbeMs / s0.ms_total)));
+    }
     const uint64_t warm = std::max<uint64_t>(P / 8, std::min<uint64_t>(P, 64));
     fbpt_tuning t = {};
     t.probe_samples = P;
     double rr_sum = 0;
     uint64_t rr_n = 0;
     // samples per second of one shape (a warm-up run on `warm` samples first)
-    auto probe = [&](uint32_t WB, uint32_t blocks, double& rate) -> int {
+    auto probe = [&](uint32_t WB, uint32_t blocks, double& rate, uint32_t sched) -> int {
         fbpt_opts q = o;
+        q.schedule = sched;
         q.words = std::min<uint32_t>(WB, 8);
         q.slots = WB / q.words;
         q.refill = FBPT_REFILL_LANE;
@@ -1924,12 +1972,14 @@ int autotune_impl(fbpt_graph* g, uint64_t seed, uint64_t S, const fbpt_opts* bas
         t.candidates += 1;
         return FBPT_OK;
     };
+    // a row width given in base (words * slots) caps the widths tried
+    const uint32_t max_wb = (base && base->words) ? base->words * (base->slots ? base->slots : 1) : kMaxWords;
     uint32_t best_wb = 1;
     double best = -1;
-    for (uint32_t WB = 1; WB <= kMaxWords; WB *= 2) {
+    for (uint32_t WB = 1; WB <= std::min(max_wb, kMaxWords); WB *= 2) {
         if (WB > 1 && 64ull * WB > P) break;
         double rate = 0;
-        FBPT_TRY(probe(WB, 0, rate));
+        FBPT_TRY(probe(WB, 0, rate, o.schedule));
         if (rate > best) {
             best = rate;
             best_wb = WB;
@@ -1941,16 +1991,35 @@ int autotune_impl(fbpt_graph* g, uint64_t seed, uint64_t S, const fbpt_opts* bas
     for (int div = 2; div <= 8; div *= 2) {
         const uint32_t blocks = (uint32_t)std::max(1, full / div);
         double rate = 0;
-        FBPT_TRY(probe(best_wb, blocks, rate));
+        FBPT_TRY(probe(best_wb, blocks, rate, o.schedule));
         if (rate >= 0.97 * best) {
             best_blocks = blocks;
             best_rate = rate;
+        }
+    }
+    // the learned schedule is judged against the degree-ratio heuristic and
+    // plain push on this graph: another one is kept only if it is at least 3%
+    // faster at the chosen shape
+    uint32_t best_sched = o.schedule;
+    if (o.schedule == FBPT_SCHED_LEARNED || o.schedule == FBPT_SCHED_HEURISTIC) {
+        const uint32_t others[2] = {o.schedule == FBPT_SCHED_LEARNED ? (uint32_t)FBPT_SCHED_HEURISTIC
+                                                                    : (uint32_t)FBPT_SCHED_LEARNED,
+                                    (uint32_t)FBPT_SCHED_PUSH};
+        for (uint32_t k = 0; k < 2; ++k) {
+            if (others[k] == FBPT_SCHED_LEARNED && !o.policy) continue;
+            double rate = 0;
+            FBPT_TRY(probe(best_wb, best_blocks, rate, others[k]));
+            if (rate > 1.03 * best_rate) {
+                best_rate = rate;
+                best_sched = others[k];
+            }
         }
     }
     t.words = std::min<uint32_t>(best_wb, 8);
     t.slots = best_wb / t.words;
     t.refill = FBPT_REFILL_LANE;
     t.blocks = best_blocks;
+    t.schedule = best_sched;
     t.probe_rate = best_rate;
     t.rr_per_sample = rr_n ? rr_sum / (double)rr_n : 0.0;
     g->tuned = t;

@@ -150,6 +150,7 @@ struct Eng {
     uint64_t m;
     uint64_t pend_cap, list_cap, chunk_cap, spill_cap;
     uint32_t unfused;
+    uint32_t alt;                 // levels may expand other than by plain push (launch k_expand_alt)
     Ctl* ctl;
     uint32_t* starts;             // S
     uint32_t* vcount;             // n

@@ -88,7 +88,8 @@ def test_batched_reruns_tasks_that_outgrow_their_buffers(fbpt):
 
 def test_autotune_probe_statistics(fbpt):
     """The tuner's RR mean is the exact mean size of the probe samples
-    (ids 0 .. min(S, 8192) - 1), and the stored shape is what it returned."""
+    (ids 0 .. P - 1, with P = S here since S <= 4096), and the stored shape
+    is what it returned."""
     g = synth.rmat_wc(12)
     dg = fbpt.Graph.from_synth(g)
     t = fbpt.autotune(dg, 5, 3000)
