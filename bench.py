@@ -85,8 +85,8 @@ class Clocks:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def build_workload():
-    w = synth.WORKLOADS[WORKLOAD]()
+def build_workload(name=WORKLOAD):
+    w = synth.WORKLOADS[name]()
     return w, w.graphs[0]
 
 
@@ -177,6 +177,8 @@ def main():
     ap.add_argument("--samples", type=int, default=1 << 20)
     ap.add_argument("--batched-steps", type=int, default=1,
                     help="timed steps of the 32-graph batched comparison (0 = skip)")
+    ap.add_argument("--workload", default=WORKLOAD, choices=["rmat_s20_wc", "rmat_s22_wc"],
+                    help="single-graph workload (profiling runs; the reported line is rmat_s22_wc)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-fused comparison on this workload")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffers) measurement")
@@ -195,9 +197,9 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     fbpt.build()
-    w, g = build_workload()
+    w, g = build_workload(args.workload)
     S = args.samples
-    k = w.k
+    k = w.k or 100
     seed = w.seeds[0]
     first = rank * S
     stream = torch.cuda.current_stream()
@@ -343,7 +345,7 @@ def main():
             "metric": METRIC, "value": value, "unit": "RR samples/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "graph": g.name, "n": g.n, "m": g.m, "samples_per_gpu": S, "k": k,
+            "config": {"workload": args.workload, "graph": g.name, "n": g.n, "m": g.m, "samples_per_gpu": S, "k": k,
                        "shape": kw, "autotuned": tuned,
                        "l2": "inputs larger than L2 (in-CSR + thresholds %.0f MB)" % ((g.m * 8 + g.n * 8) / 1e6)},
             "plain_fused": plain, "batched_32": batched,

@@ -132,6 +132,12 @@ __device__ void dev_sweep(const Eng& E, Smem& sm) {
     const uint32_t F = L2(&ctl->fin_count);
     const uint32_t spill = L2(&ctl->spill_sweep);
     if (F == 0 && !spill) return;
+    {
+        // a CTA whose first index lies beyond both entry ranges has nothing to do
+        uint64_t work = L2(&ctl->fin_pre[F]);
+        if (spill) work = max(work, min((uint64_t)L2(&ctl->spill_len[L2(&ctl->spill_cur) ^ 1u]), E.spill_cap));
+        if ((uint64_t)blockIdx.x * blockDim.x >= work) return;
+    }
     phase_begin(ctl, 2);
     __syncthreads();
     for (uint32_t k = threadIdx.x; k <= F; k += blockDim.x) sm.lane[k] = L2(&ctl->fin_pre[k]);
@@ -509,10 +515,11 @@ __device__ __forceinline__ uint32_t nth_bit64(uint64_t m, uint32_t r) {
 // units (if w has in-edges).
 __device__ void dev_commit(const Eng& E, Smem& sm) {
     Ctl* ctl = E.ctl;
+    const uint32_t P = (uint32_t)min((uint64_t)L2(&ctl->pend_count), E.pend_cap);
+    if ((uint64_t)blockIdx.x * blockDim.x >= P) return;  // no pending vertex for this CTA
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < 2 * E.WB; i += blockDim.x) sm.act[i] = 0;
     __syncthreads();
-    const uint32_t P = (uint32_t)min((uint64_t)L2(&ctl->pend_count), E.pend_cap);
     if (P) phase_begin(ctl, 1);
     const uint32_t spill_cur = L2(&ctl->spill_cur);
     const uint32_t lane = lane_id();
