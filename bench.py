@@ -29,10 +29,13 @@ sys.path.insert(0, ROOT)
 import synth  # noqa: E402
 
 WORKLOAD = "rmat_s22_wc"
-# DRAM bytes (read + write) of one steady-state k_expand launch from the ncu
-# capture summarised in profiles/k_expand_rmat_s22_wc.md; None once the kernel
-# has changed since that capture.
-EXPAND_TRAFFIC_BYTES = None
+# DRAM bytes (read + write) per 4-edge group of a steady-state k_expand
+# launch, from the ncu capture summarised in
+# profiles/level_kernels_rmat_s20_wc.md (level 40 of the R-MAT s20 WC workload
+# at 64-word rows: 55,187,712 B read + 230,400 B written for 1,496,061 groups).
+# The bench scales it by its own groups per launch; None once the kernel has
+# changed since that capture.
+EXPAND_DRAM_BYTES_PER_GROUP = (55187712 + 230400) / 1496061
 METRIC = "RR samples/s (bit-exact RR sets + greedy seeds, R-MAT s22 WC, 1,048,576 samples, k=100)"
 
 
@@ -292,7 +295,11 @@ def main():
     hbm_gbs = alg_bytes * launches / exp_s / 1e9 if exp_s > 0 else 0.0
     pk, pk_kind = peaks()
     roof = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s (int32)",
-            "frac": achieved / alu_peak, "traffic": EXPAND_TRAFFIC_BYTES, "kernel": "k_expand",
+            "frac": achieved / alu_peak,
+            "traffic": (EXPAND_DRAM_BYTES_PER_GROUP * st.groups_expanded / launches
+                        if EXPAND_DRAM_BYTES_PER_GROUP else None),
+            "traffic_note": "ncu DRAM bytes per group on the s20 capture x this run's groups per launch",
+            "kernel": "k_expand",
             "peak_kind": "derived: 152 SMs x 128 int32 lanes x 2.07 GHz",
             "launches_per_step": launches, "expand_ms_per_step": st.ms_expand,
             "algorithmic_ops_per_launch": ops_per_launch,

@@ -158,6 +158,7 @@ typedef struct fbpt_stats {
     uint64_t overflow_reruns;     /* batches re-run after the output pool grew */
     uint64_t mask_words;          /* non-zero 64-colour mask words of expanded frontier units */
     uint64_t trace_rows;          /* rows written to fbpt_opts.trace */
+    uint64_t groups_expanded;     /* 4-edge groups of the push levels' frontier units (expand work items) */
     double ms_total;              /* device time of the call on its stream (CUDA events), from
                                      the first sampling kernel to the finished CSR; workspace
                                      allocation on a graph's first use is not included */

@@ -59,7 +59,8 @@ class RRSetsC(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_uint64) for k in
                 ("levels", "batches", "push_levels", "pull_levels", "units_expanded", "edge_accesses",
-                 "philox_calls", "colour_edge_visits", "rr_total", "overflow_reruns", "mask_words", "trace_rows")] + \
+                 "philox_calls", "colour_edge_visits", "rr_total", "overflow_reruns", "mask_words", "trace_rows",
+                 "groups_expanded")] + \
                [("ms_total", ctypes.c_double), ("ms_expand", ctypes.c_double), ("ms_commit", ctypes.c_double),
                 ("ms_sweep", ctypes.c_double)]
 

@@ -957,6 +957,7 @@ __device__ void dev_schedule(const Eng& E, Smem& sm) {
         ctl->list_groups = err ? 0 : (np >> kUnitBits);
         atomicAdd(&ctl->st_units, np & kUnitMask);
         if (h.list_groups != 0) atomicAdd(h.dir == kDirPull ? &ctl->st_pull : &ctl->st_push, 1ull);
+        if (h.dir != kDirPull) atomicAdd(&ctl->st_groups, h.list_groups);
         ctl->dir = sm.dir;
         ctl->frontier_lanes = nstill;
         for (int p = 0; p < 3; ++p) {
@@ -1713,6 +1714,7 @@ int run_finish(Run& r, fbpt_stats* stats) {
         stats->colour_edge_visits += cev;
         stats->rr_total += total;
         stats->mask_words += H->st_mask_words;
+        stats->groups_expanded += H->st_groups;
         stats->ms_expand += 1e-6 * (double)H->st_phase_ns[0];
         stats->ms_commit += 1e-6 * (double)H->st_phase_ns[1];
         stats->ms_sweep += 1e-6 * (double)H->st_phase_ns[2];

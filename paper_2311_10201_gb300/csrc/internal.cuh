@@ -81,6 +81,7 @@ struct Ctl {
     unsigned long long spill_len[2];
     // counters
     unsigned long long st_edges, st_calls, st_units, st_cev, st_assigned, st_push, st_pull, st_mask_words;
+    unsigned long long st_groups;
     unsigned long long new_colours, list_colours;  // colour bits of the new / current frontier units
     // phase times: first CTA start .. last CTA end of each phase (%globaltimer, ns);
     // index 0 expand, 1 commit, 2 sweep
