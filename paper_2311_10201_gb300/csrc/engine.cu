@@ -122,9 +122,20 @@ __device__ __forceinline__ void or_next(const Eng& E, uint32_t w, uint32_t i, ui
 // goes to position p of that range (vertices in discovery order; the final
 // CSR pass sorts each row).  The lane's bit is cleared from visited[] so that
 // the lane can carry its next sample.
-__device__ __forceinline__ void sweep_entry(const Eng& E, uint32_t l, uint32_t v) {
-    atomicAnd((unsigned long long*)&E.visited[(uint64_t)v * E.WB + (l >> 6)], ~(1ull << (l & 63)));
-    atomicAdd(&E.vcount[v], 1u);
+// The finished lanes' bits of one word of visited[v] are cleared and counted
+// once per (vertex, word), by the entry of the lowest finished lane the word
+// still holds: when many lanes that share a word end together (their RR sets
+// overlapping in a giant component), one atomic per word replaces one per lane.
+// Only that entry writes the word during the sweep, so every other entry of
+// the word reads either all of the finished bits (and is not the lowest) or
+// none of them.
+__device__ __forceinline__ void sweep_entry(const Eng& E, const uint64_t* fin, uint32_t l, uint32_t v) {
+    const uint32_t w = l >> 6;
+    unsigned long long* p = (unsigned long long*)&E.visited[(uint64_t)v * E.WB + w];
+    const uint64_t m = L2(p) & fin[w];
+    if (m == 0 || (uint32_t)(__ffsll((long long)m) - 1) != (l & 63u)) return;
+    atomicAnd(p, ~(unsigned long long)m);
+    atomicAdd(&E.vcount[v], (uint32_t)__popcll(m));
 }
 
 __device__ void dev_sweep(const Eng& E, Smem& sm) {
@@ -161,7 +172,7 @@ __device__ void dev_sweep(const Eng& E, Smem& sm) {
             const uint32_t v = L2(&E.seg[(uint64_t)l * E.seg_cap + p]);
             const uint64_t dst = L2(&ctl->lane_base[l]) + p;
             if (dst < cap) E.rows_v[dst] = v;
-            sweep_entry(E, l, v);
+            sweep_entry(E, sm.fin, l, v);
         }
     }
     if (spill) {
@@ -185,7 +196,7 @@ __device__ void dev_sweep(const Eng& E, Smem& sm) {
             if (ok && done) {
                 const uint64_t d = L2(&ctl->lane_base[l]) + p;
                 if (d < cap) E.rows_v[d] = v;
-                sweep_entry(E, l, v);
+                sweep_entry(E, sm.fin, l, v);
             } else if (ok) {
                 if (kp < E.spill_cap) E.spill[(uint64_t)dst * E.spill_cap + kp] = ent;
                 else atomicOr(&ctl->error, (unsigned)kErrSpillOverflow);
