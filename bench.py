@@ -278,6 +278,19 @@ def main():
         plain = {"value": S / (pms / 1e3), "unit": "RR samples/s", "ms_per_step": pms, "steps": psteps,
                  "shape": plain_kw, "speedup": (S / (ms_step / 1e3)) / (S / (pms / 1e3))}
 
+    # ---- the consumer of the path: IMM seed selection (k = 100, epsilon = 0.1,
+    # ell = 1) on the same graph and shape, sampling and greedy included ----
+    imm = None
+    if rank == 0 and world == 1 and not args.no_plain:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, _, ires, ist = fbpt.imm(dg, k, 0.1, 1.0, seed, **kw)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        imm = {"k": k, "epsilon": 0.1, "ell": 1.0, "seconds": dt, "samples": ires["samples"],
+               "theta": ires["theta"], "rounds": ires["rounds"], "lower_bound": ires["lower_bound"],
+               "coverage": ires["coverage"], "samples_per_s": ires["samples"] / dt}
+
     batched = None
     if rank == 0 and world == 1 and args.batched_steps > 0:
         batched = bench_batched(fbpt, torch, stream, args.batched_steps, args.schedule)
@@ -355,7 +368,7 @@ def main():
             "config": {"workload": args.workload, "graph": g.name, "n": g.n, "m": g.m, "samples_per_gpu": S, "k": k,
                        "shape": kw, "autotuned": tuned,
                        "l2": "inputs larger than L2 (in-CSR + thresholds %.0f MB)" % ((g.m * 8 + g.n * 8) / 1e6)},
-            "plain_fused": plain, "batched_32": batched,
+            "plain_fused": plain, "batched_32": batched, "imm": imm,
             "colour_edge_visits_per_s": st.colour_edge_visits * world / (ms_step / 1e3),
             "stats": st.as_dict(),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,

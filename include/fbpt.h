@@ -265,6 +265,44 @@ int fbpt_select_seeds(const fbpt_rrsets* rr, uint32_t k, uint32_t* seeds_host, u
  * Work runs on rr->stream; the call returns after it finishes. */
 int fbpt_select_seeds_noalloc(const fbpt_rrsets* rr, uint32_t k, uint32_t* seeds_host, uint64_t* gains_host);
 
+/* ---- Influence maximization: the IMM sampling loop -------------------------------
+ * The consumer of the sampler that Section 2 describes: IMM (Tang, Shi and
+ * Xiao, SIGMOD 2015) fixes the number of RR sets theta that gives a
+ * (1 - 1/e - epsilon)-approximate seed set with probability at least
+ * 1 - n^-ell, then runs greedy max-k-cover over them.  With natural logs,
+ * ell' = ell * (1 + ln 2 / ln n), eps' = sqrt(2) * epsilon and
+ * L = ln C(n, k) (the sum over i < min(k, n - k) of ln((n - i) / (i + 1))):
+ *   lambda' = (2 + 2 eps'/3) (L + ell' ln n + ln log2 n) n / eps'^2,
+ *   lambda* = 2 n ((1 - 1/e) alpha + beta)^2 / epsilon^2 with
+ *             alpha = sqrt(ell' ln n + ln 2), beta = sqrt((1 - 1/e)(L + ell' ln n + ln 2)).
+ * Rounds i = 1 .. ceil(log2 n) - 1: x = n / 2^i; the sample holds
+ * theta_i = ceil(lambda' / x) RR sets (sample ids 0 .. theta_i - 1 under seed,
+ * extended, never redrawn); greedy picks k seeds covering a fraction F of
+ * them; if n F >= (1 + eps') x the lower bound is LB = n F / (1 + eps') and
+ * the rounds stop (LB = 1 if no round succeeds).  Then theta =
+ * ceil(lambda* / LB), the sample is extended to max(its size, theta) and the
+ * greedy seeds over it are the result.  Every sampling step is fbpt_sample
+ * with opts, every selection fbpt_select_seeds.
+ *
+ * Needs n >= 2, 1 <= k <= n, epsilon > 0, ell > 0.  max_samples (0 = none)
+ * caps the sample: FBPT_EINVAL, naming the size, if a round or theta needs
+ * more.  seeds_host[k] and gains_host[k] (may be NULL) receive the final
+ * picks; result (may be NULL) the sizes and bounds; stats (may be NULL)
+ * accumulates over every sampling call. */
+typedef struct fbpt_imm_result {
+    uint64_t theta;       /* ceil(lambda* / LB) */
+    uint64_t samples;     /* RR sets the final selection used: max(theta, the last round's theta_i) */
+    double lower_bound;   /* LB */
+    double coverage;      /* fraction of those RR sets the seeds cover */
+    double lambda_prime, lambda_star;
+    uint32_t rounds;      /* estimation rounds run */
+    uint32_t reserved;
+} fbpt_imm_result;
+
+int fbpt_imm(fbpt_graph* g, uint32_t k, double epsilon, double ell, uint64_t seed, uint64_t max_samples,
+             const fbpt_opts* opts, uint32_t* seeds_host, uint64_t* gains_host, fbpt_imm_result* result,
+             fbpt_stats* stats);
+
 /* ---- Schedule policy --------------------------------------------------------------
  * A 6 -> 32 -> 32 -> 8 ReLU network (FP32) that picks, per level, how the
  * level expands (Section 9 (a): direction switching among push, push that

@@ -50,6 +50,15 @@ class Tuning(ctypes.Structure):
         return d
 
 
+class ImmResult(ctypes.Structure):
+    _fields_ = [("theta", ctypes.c_uint64), ("samples", ctypes.c_uint64), ("lower_bound", ctypes.c_double),
+                ("coverage", ctypes.c_double), ("lambda_prime", ctypes.c_double), ("lambda_star", ctypes.c_double),
+                ("rounds", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
 class RRSetsC(ctypes.Structure):
     _fields_ = [("S", ctypes.c_uint64), ("total", ctypes.c_uint64), ("n", ctypes.c_uint32),
                 ("offsets", ctypes.c_void_p), ("verts", ctypes.c_void_p), ("starts", ctypes.c_void_p),
@@ -97,6 +106,9 @@ _SIGS = {
     "fbpt_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.POINTER(Opts),
                                      ctypes.POINTER(Tuning)]),
     "fbpt_graph_tuning": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Tuning)]),
+    "fbpt_imm": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
+                                ctypes.c_uint64, ctypes.POINTER(Opts), U32P, U64P, ctypes.POINTER(ImmResult),
+                                ctypes.POINTER(Stats)]),
     "fbpt_rrsets_copy_rows": (ctypes.c_int, [ctypes.POINTER(RRSetsC), ctypes.c_uint64, ctypes.c_uint64, U64P, U32P,
                                              ctypes.c_uint64]),
     "fbpt_rrsets_free": (ctypes.c_int, [ctypes.POINTER(RRSetsC)]),
@@ -338,6 +350,18 @@ def tuning(g: Graph) -> dict:
     t = Tuning()
     _check(lib().fbpt_graph_tuning(g._h, ctypes.byref(t)))
     return t.as_dict()
+
+
+def imm(g: Graph, k: int, epsilon: float, ell: float, seed: int, max_samples: int = 0, **kw):
+    """IMM seed selection (fbpt_imm): (seeds[k], gains[k], result dict, Stats)."""
+    o = make_opts(stream=g.stream, **kw)
+    seeds = np.zeros(max(k, 1), np.uint32)
+    gains = np.zeros(max(k, 1), np.uint64)
+    res = ImmResult()
+    st = Stats()
+    _check(lib().fbpt_imm(g._h, k, float(epsilon), float(ell), seed, max_samples, ctypes.byref(o),
+                          _ptr_u32(seeds), _ptr_u64(gains), ctypes.byref(res), ctypes.byref(st)))
+    return seeds[:k], gains[:k], res.as_dict(), st
 
 
 def select_seeds(rr: RRSets, k: int):

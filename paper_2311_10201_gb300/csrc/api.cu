@@ -80,6 +80,16 @@ extern "C" int fbpt_autotune(fbpt_graph* g, uint64_t seed, uint64_t S, const fbp
     }
 }
 
+extern "C" int fbpt_imm(fbpt_graph* g, uint32_t k, double epsilon, double ell, uint64_t seed, uint64_t max_samples,
+                        const fbpt_opts* opts, uint32_t* seeds_host, uint64_t* gains_host, fbpt_imm_result* result,
+                        fbpt_stats* stats) {
+    try {
+        return imm_impl(g, k, epsilon, ell, seed, max_samples, opts, seeds_host, gains_host, result, stats);
+    } catch (const std::exception& e) {
+        return fail(FBPT_ENOMEM, std::string("fbpt_imm: ") + e.what());
+    }
+}
+
 extern "C" int fbpt_graph_tuning(const fbpt_graph* g, fbpt_tuning* out) {
     if (!g || !out) return fail(FBPT_EINVAL, "fbpt_graph_tuning: null argument");
     if (!g->tuned_valid) return fail(FBPT_EINVAL, "fbpt_graph_tuning: graph was never tuned");

@@ -200,6 +200,9 @@ int sample_impl(fbpt_graph* g, uint64_t seed, uint64_t first_id, uint64_t S, con
 int sample_batched_impl(uint32_t G, fbpt_graph* const* gs, const uint64_t* seeds, const uint64_t* first_ids,
                         const uint64_t* Ss, const fbpt_opts* opts, fbpt_rrsets* outs, fbpt_stats* stats);
 int autotune_impl(fbpt_graph* g, uint64_t seed, uint64_t S, const fbpt_opts* base, fbpt_tuning* out);
+int imm_impl(fbpt_graph* g, uint32_t k, double epsilon, double ell, uint64_t seed, uint64_t max_samples,
+             const fbpt_opts* opts, uint32_t* seeds_host, uint64_t* gains_host, fbpt_imm_result* result,
+             fbpt_stats* stats);
 // Builds g's out-edge CSR if it is not there yet (FBPT_EUNSUPPORTED for m >= 2^32).
 int ensure_out_csr(fbpt_graph* g, cudaStream_t st);
 // Device-wide exclusive scan of n counts into n+1 uint64 offsets (out[n] = total).
