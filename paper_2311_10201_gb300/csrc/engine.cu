@@ -56,6 +56,15 @@ __device__ __forceinline__ uint64_t row_groups(uint64_t rs, uint64_t re) {
 template <typename T>
 __device__ __forceinline__ T L2(const T* p) { return __ldcg(p); }
 
+// Loads of data no kernel writes while the expand runs (frontier list, chunk
+// map, stage words): through the read-only cache in the per-level kernels,
+// through L2 in the persistent kernel, whose levels rewrite them in place.
+template <bool ro, typename T>
+__device__ __forceinline__ T LD(const T* p) {
+    if constexpr (ro) return __ldg(p);
+    else return __ldcg(p);
+}
+
 // Commit scratch of one warp: its 32 pending vertices and what their words add.
 struct CommitWarp {
     uint64_t m[32];                 // words of next[w] that changed this level
@@ -238,11 +247,12 @@ struct Grp {
     uint32_t sure;     // of those, edges that are always live
 };
 
+template <bool ro>
 __device__ __forceinline__ bool grp_load(const Eng& E, uint32_t u, uint64_t j, Grp& G, uint64_t& n_edges) {
-    G.occ = L2(&E.list_occ[u]);
-    G.mrow = L2(&E.list_mrow[u]);
-    const uint64_t rs = L2(&E.list_rs[u]), re = L2(&E.list_re[u]);
-    G.only = E.unfused ? L2(&E.list_only[u]) : 0u;
+    G.occ = LD<ro>(&E.list_occ[u]);
+    G.mrow = LD<ro>(&E.list_mrow[u]);
+    const uint64_t rs = LD<ro>(&E.list_rs[u]), re = LD<ro>(&E.list_re[u]);
+    G.only = E.unfused ? LD<ro>(&E.list_only[u]) : 0u;
     G.q = (rs >> 2) + j;
     G.c4 = __ldg(reinterpret_cast<const uint4*>(E.col) + G.q);
     const uint4 t = __ldg(reinterpret_cast<const uint4*>(E.thr) + G.q);
@@ -259,7 +269,7 @@ __device__ __forceinline__ bool grp_load(const Eng& E, uint32_t u, uint64_t j, G
     return inrow != 0;
 }
 
-template <bool filtered>
+template <bool filtered, bool ro>
 __device__ __forceinline__ void grp_run(const Eng& E, const uint32_t* lane_j, const Grp& G, const PhiloxKeys& K,
                                         uint64_t& n_calls) {
     const bool need = (G.valid & ~G.sure) != 0;  // some edge needs a draw
@@ -269,7 +279,7 @@ __device__ __forceinline__ void grp_run(const Eng& E, const uint32_t* lane_j, co
     while (words) {
         const uint32_t i = __ffsll((long long)words) - 1;
         words &= words - 1;
-        uint64_t x = G.only ? (1ull << ((G.only - 1u) & 63u)) : L2(&E.stage[(uint64_t)G.mrow * E.WB + i]);
+        uint64_t x = G.only ? (1ull << ((G.only - 1u) & 63u)) : LD<ro>(&E.stage[(uint64_t)G.mrow * E.WB + i]);
         // filtered push: a colour the source has already seen needs no draw
         uint64_t v0 = ~0ull, v1 = ~0ull, v2 = ~0ull, v3 = ~0ull;
         if (filtered) {
@@ -327,13 +337,14 @@ __device__ __forceinline__ void grp_run(const Eng& E, const uint32_t* lane_j, co
 // The unit holding group g of chunk c: chunk_u0[c] names the unit holding
 // group 32c; the lanes find their own unit among the (at most 32) units of the
 // chunk by binary lifting over shuffled group offsets.  All lanes must call.
+template <bool ro>
 __device__ __forceinline__ uint32_t chunk_unit(const Eng& E, uint32_t c, uint64_t nchunks, uint64_t U, uint64_t g,
                                                uint64_t& j) {
     const uint32_t lane = lane_id();
-    const uint32_t u0 = L2(&E.chunk_u0[c]);
-    const uint32_t ul = (c + 1 < nchunks) ? L2(&E.chunk_u0[c + 1]) : (uint32_t)(U - 1);
+    const uint32_t u0 = LD<ro>(&E.chunk_u0[c]);
+    const uint32_t ul = (c + 1 < nchunks) ? LD<ro>(&E.chunk_u0[c + 1]) : (uint32_t)(U - 1);
     const uint32_t nu = min(ul - u0 + 1u, 32u);
-    const uint64_t gb = lane < nu ? L2(&E.list_g[u0 + lane]) : ~0ull;
+    const uint64_t gb = lane < nu ? LD<ro>(&E.list_g[u0 + lane]) : ~0ull;
     uint32_t k = 0;
 #pragma unroll
     for (uint32_t step = 16; step > 0; step >>= 1) {
@@ -426,7 +437,7 @@ __device__ __forceinline__ void dev_pull(const Eng& E, const uint32_t* lane_j, c
 // takes kChunksPerGrab chunks of 32 consecutive groups per atomic, one group
 // per lane (FBPT_EXPAND_ILP chunks at a time).  One instance per push variant,
 // so that the plain push loop carries no register of the filtered one.
-template <bool filtered>
+template <bool filtered, bool ro>
 __device__ __forceinline__ void expand_push(const Eng& E, const uint32_t* lane_j, const PhiloxKeys& K, uint64_t G,
                                             uint64_t U, uint64_t nchunks, uint64_t& n_edges, uint64_t& n_calls) {
     Ctl* ctl = E.ctl;
@@ -442,14 +453,14 @@ __device__ __forceinline__ void expand_push(const Eng& E, const uint32_t* lane_j
             const uint64_t ga = (uint64_t)c * kChunk + lane;
             const uint64_t gbb = ga + kChunk;
             uint64_t ja = 0, jb = 0;
-            const uint32_t ua = chunk_unit(E, c, nchunks, U, ga, ja);
+            const uint32_t ua = chunk_unit<ro>(E, c, nchunks, U, ga, ja);
             uint32_t ub = 0;
-            if (two) ub = chunk_unit(E, c + 1, nchunks, U, gbb, jb);
+            if (two) ub = chunk_unit<ro>(E, c + 1, nchunks, U, gbb, jb);
             Grp A, B;
-            const bool la = ga < G && grp_load(E, ua, ja, A, n_edges);
-            const bool lb = two && gbb < G && grp_load(E, ub, jb, B, n_edges);
-            if (la) grp_run<filtered>(E, lane_j, A, K, n_calls);
-            if (lb) grp_run<filtered>(E, lane_j, B, K, n_calls);
+            const bool la = ga < G && grp_load<ro>(E, ua, ja, A, n_edges);
+            const bool lb = two && gbb < G && grp_load<ro>(E, ub, jb, B, n_edges);
+            if (la) grp_run<filtered, ro>(E, lane_j, A, K, n_calls);
+            if (lb) grp_run<filtered, ro>(E, lane_j, B, K, n_calls);
         }
     }
 }
@@ -480,8 +491,10 @@ __device__ void dev_expand(const Eng& E, uint32_t* lane_j) {
     const PhiloxKeys K = philox_keys(E.seed);
     uint64_t n_edges = 0, n_calls = 0;
     if (part != kPartPush && pull) dev_pull(E, lane_j, K, n_edges, n_calls);
-    else if (part != kPartPush && dir == kDirFiltered) expand_push<true>(E, lane_j, K, G, U, nchunks, n_edges, n_calls);
-    else if (part != kPartAlt) expand_push<false>(E, lane_j, K, G, U, nchunks, n_edges, n_calls);
+    else if (part != kPartPush && dir == kDirFiltered)
+        expand_push<true, part != kPartAll>(E, lane_j, K, G, U, nchunks, n_edges, n_calls);
+    else if (part != kPartAlt)
+        expand_push<false, part != kPartAll>(E, lane_j, K, G, U, nchunks, n_edges, n_calls);
     n_edges = warp_sum(n_edges);
     n_calls = warp_sum(n_calls);
     if (lane == 0) {
