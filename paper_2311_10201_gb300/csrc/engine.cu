@@ -540,7 +540,11 @@ __device__ __forceinline__ uint32_t nth_bit64(uint64_t m, uint32_t r) {
 __device__ void dev_commit(const Eng& E, Smem& sm) {
     Ctl* ctl = E.ctl;
     const uint32_t P = (uint32_t)min((uint64_t)L2(&ctl->pend_count), E.pend_cap);
-    if ((uint64_t)blockIdx.x * blockDim.x >= P) return;  // no pending vertex for this CTA
+    // vertices per warp: spread a small level over every warp of the grid (the
+    // work is a chain of dependent loads per vertex), up to one per lane
+    const uint64_t nwarp = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const uint32_t vpw = (uint32_t)min((uint64_t)32, max((uint64_t)1, (P + nwarp - 1) / nwarp));
+    if ((uint64_t)blockIdx.x * (blockDim.x >> 5) * vpw >= P) return;  // no pending vertex for this CTA
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < 2 * E.WB; i += blockDim.x) sm.act[i] = 0;
     __syncthreads();
@@ -548,12 +552,11 @@ __device__ void dev_commit(const Eng& E, Smem& sm) {
     const uint32_t spill_cur = L2(&ctl->spill_cur);
     const uint32_t lane = lane_id();
     const uint64_t wid = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint64_t nwarp = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     CommitWarp& cw = sm.cw[threadIdx.x >> 5];
     uint64_t mwords = 0, ncol = 0;
-    for (uint64_t base = wid * 32; base < P; base += nwarp * 32) {
+    for (uint64_t base = wid * vpw; base < P; base += nwarp * vpw) {
         const uint64_t idx = base + lane;
-        const bool ok = idx < P;
+        const bool ok = lane < vpw && idx < P;
         uint32_t w = 0;
         uint64_t m = 0, rs = 0, re = 0;
         if (ok) {
