@@ -92,6 +92,20 @@ enum fbpt_refill {
                               algorithm with 64 * words * slots colours per group */
 };
 
+/* Diffusion model of the RR sets (Section 2 names IC and LT). */
+enum fbpt_model {
+    FBPT_MODEL_IC = 0,  /* independent cascade: edge e live for sample s by its own draw (contract above) */
+    FBPT_MODEL_LT = 1   /* linear threshold, live-edge form: each vertex keeps at most one in-edge.
+                           thr[e] is the weight w(e) = thr[e] / 2^32 (0xFFFFFFFF read as 1), and a
+                           row's weights must sum to at most 1 (FBPT_EINVAL otherwise).  For sample
+                           s, vertex v draws r = out[0] of Philox(ctr = (lo32(s), hi32(s), v,
+                           0x40000000)) and keeps the first edge e of its row with
+                           r < w(first) + ... + w(e) (in units of 2^-32), none if r is beyond the
+                           row's total.  The RR set of s is the walk start(s) <- u1 <- u2 ... along
+                           the kept in-edges, ending at a vertex that kept none or at one already
+                           on the walk.  Levels are push only; the unfused form is not offered */
+};
+
 /* One row per level of a sampling run, filled when fbpt_opts.trace is set.
  * The schedule policy is trained on these rows (features of a level and the
  * time each phase took). */
@@ -124,6 +138,7 @@ typedef struct fbpt_opts {
     uint32_t refill;     /* enum fbpt_refill */
     uint32_t blocks;     /* CTAs of each level kernel; 0 = every CTA the GPU holds at once.
                             Fewer leave room for other graphs of a batched run */
+    uint32_t model;      /* enum fbpt_model (0 = IC) */
     const fbpt_policy* policy; /* used by FBPT_SCHED_LEARNED; NULL = built-in heuristic */
     void* stream;        /* cudaStream_t */
     uint64_t spin_limit; /* FBPT_LAUNCH_PERSISTENT: polls before a grid-barrier wait gives up

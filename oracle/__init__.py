@@ -56,6 +56,12 @@ def _load():
         lib.oracle_rr.argtypes = [ctypes.c_uint32, U64P, U32P, U32P, ctypes.c_uint64, ctypes.c_uint64, U64P,
                                   ctypes.c_uint64, ctypes.c_int, ctypes.POINTER(U64P), ctypes.POINTER(U32P), U32P]
         lib.oracle_rr.restype = ctypes.c_int
+        lib.oracle_rr_lt.argtypes = lib.oracle_rr.argtypes
+        lib.oracle_rr_lt.restype = ctypes.c_int
+        lib.oracle_vertex_draw.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32]
+        lib.oracle_vertex_draw.restype = ctypes.c_uint32
+        lib.oracle_lt_choice.argtypes = [U64P, U32P, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32]
+        lib.oracle_lt_choice.restype = ctypes.c_int64
         lib.oracle_rr_fused.argtypes = [ctypes.c_uint32, U64P, U32P, U32P, ctypes.c_uint64, ctypes.c_uint64,
                                         ctypes.c_uint64, ctypes.c_uint32, ctypes.POINTER(U64P),
                                         ctypes.POINTER(U32P), U64P]
@@ -123,21 +129,34 @@ def _take(offp, vertp, count):
     return off, verts
 
 
-def rr_sets(g, seed: int, first_id: int = 0, count: int | None = None, ids=None, nthreads: int = 0) -> RRSets:
-    """Definition 2: one BFS per sample over in-edges with hashed liveness."""
+def rr_sets(g, seed: int, first_id: int = 0, count: int | None = None, ids=None, nthreads: int = 0,
+            model: str = "ic") -> RRSets:
+    """Definition 2: one BFS per sample over in-edges with hashed liveness
+    (model "ic"), or one reverse walk over the kept in-edges (model "lt")."""
     lib = _load()
+    fn = {"ic": lib.oracle_rr, "lt": lib.oracle_rr_lt}[model]
     if ids is not None:
         ids = np.ascontiguousarray(ids, dtype=np.uint64)
         count = ids.size
     offp, vertp = U64P(), U32P()
     starts = np.zeros(max(count, 1), np.uint32)
-    rc = lib.oracle_rr(g.n, _p(g.row_ptr, ctypes.c_uint64), _p(g.col, ctypes.c_uint32), _p(g.thr, ctypes.c_uint32),
-                       seed, first_id, _p(ids, ctypes.c_uint64) if ids is not None else None, count, nthreads,
-                       ctypes.byref(offp), ctypes.byref(vertp), _p(starts, ctypes.c_uint32))
+    rc = fn(g.n, _p(g.row_ptr, ctypes.c_uint64), _p(g.col, ctypes.c_uint32), _p(g.thr, ctypes.c_uint32),
+            seed, first_id, _p(ids, ctypes.c_uint64) if ids is not None else None, count, nthreads,
+            ctypes.byref(offp), ctypes.byref(vertp), _p(starts, ctypes.c_uint32))
     if rc != 0:
         raise MemoryError("oracle_rr failed")
     off, verts = _take(offp, vertp, count)
     return RRSets(off, verts, starts[:count])
+
+
+def vertex_draw(seed: int, s: int, v: int) -> int:
+    """The LT model's draw of vertex v for sample s."""
+    return int(_load().oracle_vertex_draw(seed, s, v))
+
+
+def lt_choice(g, seed: int, s: int, v: int) -> int:
+    """The in-edge v keeps for sample s under LT, or -1."""
+    return int(_load().oracle_lt_choice(_p(g.row_ptr, ctypes.c_uint64), _p(g.thr, ctypes.c_uint32), seed, s, v))
 
 
 def rr_sets_fused(g, seed: int, first_id: int, count: int, W: int = 1):

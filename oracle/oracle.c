@@ -39,6 +39,17 @@
  *    also counts edge accesses (one per edge scanned per processing of an
  *    active vertex), the quantity Theorem 1 bounds.
  *
+ *  - oracle_rr_lt: RR sets under the linear-threshold (LT) model (Section 2
+ *    names IC and LT; Kempe et al.'s live-edge form of LT): each vertex v
+ *    keeps at most one in-edge, edge e of its row with probability
+ *    w(e) = thr[e] / 2^32 (0xFFFFFFFF read as 1), none with the rest.  For
+ *    sample s the choice is one Philox draw r = out[0] of the counter
+ *    (lo(s), hi(s), v, 0x40000000): the first edge e of the row with
+ *    r < w(rs) + ... + w(e) (sums in units of 2^-32), none if r is beyond the
+ *    row's total.  The RR set of s is the walk start(s) <- u1 <- u2 ... along
+ *    the chosen in-edges, which ends at a vertex with no edge or at a vertex
+ *    already on the walk.
+ *
  *  - oracle_greedy: greedy maximum k-coverage over the RR sets (Section 2:
  *    seed selection reduces to max-k-cover).  Each round recounts, for every
  *    vertex, the RR sets that contain it and are not yet covered, and takes
@@ -154,14 +165,56 @@ static uint64_t rr_one(uint32_t n, const uint64_t* row_ptr, const uint32_t* col,
     return out->len - base;
 }
 
+/* ---- The linear-threshold model: one reverse walk per sample --------------- */
+
+uint32_t oracle_vertex_draw(uint64_t seed, uint64_t s, uint32_t v) {
+    uint32_t ctr[4] = {(uint32_t)s, (uint32_t)(s >> 32), v, 0x40000000u};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t out[4];
+    oracle_philox(ctr, key, out);
+    return out[0];
+}
+
+/* The in-edge vertex v keeps for sample s, or -1 for none. */
+int64_t oracle_lt_choice(const uint64_t* row_ptr, const uint32_t* thr, uint64_t seed, uint64_t s, uint32_t v) {
+    const uint64_t r = oracle_vertex_draw(seed, s, v);
+    uint64_t acc = 0;
+    for (uint64_t e = row_ptr[v]; e < row_ptr[v + 1]; ++e) {
+        acc += thr[e] == 0xFFFFFFFFu ? (1ull << 32) : (uint64_t)thr[e];
+        if (r < acc) return (int64_t)e;
+    }
+    return -1;
+}
+
+static uint64_t rr_one_lt(uint32_t n, const uint64_t* row_ptr, const uint32_t* col, const uint32_t* thr,
+                          uint64_t seed, uint64_t s, uint64_t* mark, uint64_t tag, vec32* queue,
+                          vec32* out, uint32_t* start_out) {
+    uint32_t v = oracle_start(seed, s, n);
+    if (start_out) *start_out = v;
+    queue->len = 0;
+    for (;;) {
+        vec_push(queue, v);
+        mark[v] = tag;
+        const int64_t e = oracle_lt_choice(row_ptr, thr, seed, s, v);
+        if (e < 0) break;
+        const uint32_t u = col[e];
+        if (mark[u] == tag) break;
+        v = u;
+    }
+    qsort(queue->data, queue->len, sizeof(uint32_t), cmp_u32);
+    uint64_t base = out->len;
+    for (uint64_t i = 0; i < queue->len; ++i) vec_push(out, queue->data[i]);
+    return out->len - base;
+}
+
 /* RR sets for `count` samples.  Sample j has id ids[j] when ids is non-NULL,
  * else first_id + j.  On success *offsets_out (count+1 entries) and *verts_out
  * are malloc'd (free with oracle_free); starts_out (count entries) is
  * optional.  threads <= 0 uses the OpenMP default.  Returns 0, or -1 when
  * memory runs out. */
-int oracle_rr(uint32_t n, const uint64_t* row_ptr, const uint32_t* col, const uint32_t* thr,
-              uint64_t seed, uint64_t first_id, const uint64_t* ids, uint64_t count, int threads,
-              uint64_t** offsets_out, uint32_t** verts_out, uint32_t* starts_out) {
+static int rr_many(int lt, uint32_t n, const uint64_t* row_ptr, const uint32_t* col, const uint32_t* thr,
+                   uint64_t seed, uint64_t first_id, const uint64_t* ids, uint64_t count, int threads,
+                   uint64_t** offsets_out, uint32_t** verts_out, uint32_t* starts_out) {
     const uint64_t CH = 256;
     uint64_t nchunks = (count + CH - 1) / CH;
     vec32* chunk = (vec32*)calloc(nchunks ? nchunks : 1, sizeof(vec32));
@@ -182,8 +235,8 @@ int oracle_rr(uint32_t n, const uint64_t* row_ptr, const uint32_t* col, const ui
             if (!mark) { fail = 1; continue; }
             for (uint64_t j = (uint64_t)c * CH; j < count && j < (uint64_t)(c + 1) * CH; ++j) {
                 uint64_t s = ids ? ids[j] : first_id + j;
-                sizes[j] = rr_one(n, row_ptr, col, thr, seed, s, mark, j + 1, &queue, &chunk[c],
-                                  starts_out ? &starts_out[j] : NULL);
+                sizes[j] = (lt ? rr_one_lt : rr_one)(n, row_ptr, col, thr, seed, s, mark, j + 1, &queue, &chunk[c],
+                                                     starts_out ? &starts_out[j] : NULL);
             }
         }
         free(mark);
@@ -205,6 +258,19 @@ int oracle_rr(uint32_t n, const uint64_t* row_ptr, const uint32_t* col, const ui
     *offsets_out = off;
     *verts_out = verts;
     return 0;
+}
+
+int oracle_rr(uint32_t n, const uint64_t* row_ptr, const uint32_t* col, const uint32_t* thr,
+              uint64_t seed, uint64_t first_id, const uint64_t* ids, uint64_t count, int threads,
+              uint64_t** offsets_out, uint32_t** verts_out, uint32_t* starts_out) {
+    return rr_many(0, n, row_ptr, col, thr, seed, first_id, ids, count, threads, offsets_out, verts_out, starts_out);
+}
+
+/* As oracle_rr, under the linear-threshold model (one reverse walk per sample). */
+int oracle_rr_lt(uint32_t n, const uint64_t* row_ptr, const uint32_t* col, const uint32_t* thr,
+                 uint64_t seed, uint64_t first_id, const uint64_t* ids, uint64_t count, int threads,
+                 uint64_t** offsets_out, uint32_t** verts_out, uint32_t* starts_out) {
+    return rr_many(1, n, row_ptr, col, thr, seed, first_id, ids, count, threads, offsets_out, verts_out, starts_out);
 }
 
 void oracle_free(void* p) { free(p); }

@@ -33,14 +33,14 @@ U32P = ctypes.POINTER(ctypes.c_uint32)
 class Opts(ctypes.Structure):
     _fields_ = [("words", ctypes.c_uint32), ("slots", ctypes.c_uint32), ("schedule", ctypes.c_uint32),
                 ("launch", ctypes.c_uint32), ("unfused", ctypes.c_uint32), ("refill", ctypes.c_uint32),
-                ("blocks", ctypes.c_uint32),
+                ("blocks", ctypes.c_uint32), ("model", ctypes.c_uint32),
                 ("policy", ctypes.c_void_p), ("stream", ctypes.c_void_p), ("spin_limit", ctypes.c_uint64),
                 ("trace", ctypes.c_void_p), ("trace_cap", ctypes.c_uint64)]
 
 
 class Tuning(ctypes.Structure):
     _fields_ = [("words", ctypes.c_uint32), ("slots", ctypes.c_uint32), ("refill", ctypes.c_uint32),
-                ("blocks", ctypes.c_uint32), ("candidates", ctypes.c_uint32), ("schedule", ctypes.c_uint32),
+                ("blocks", ctypes.c_uint32), ("model", ctypes.c_uint32), ("candidates", ctypes.c_uint32), ("schedule", ctypes.c_uint32),
                 ("probe_samples", ctypes.c_uint64), ("probe_rate", ctypes.c_double),
                 ("rr_per_sample", ctypes.c_double)]
 
@@ -284,10 +284,14 @@ class RRSets:
 REFILL = {"lane": 0, "batch": 1}
 
 
+MODEL = {"ic": 0, "lt": 1}
+
+
 def make_opts(words=0, slots=0, schedule="push", launch="persistent", unfused=False, stream=None, policy=None,
-              spin_limit=0, refill="lane", blocks=0):
+              spin_limit=0, refill="lane", blocks=0, model="ic"):
     o = Opts()
     o.blocks = int(blocks)
+    o.model = MODEL[model] if isinstance(model, str) else int(model)
     o.refill = REFILL[refill] if isinstance(refill, str) else int(refill)
     o.spin_limit = int(spin_limit)
     o.words, o.slots = int(words), int(slots)

@@ -465,6 +465,52 @@ __device__ __forceinline__ void expand_push(const Eng& E, const uint32_t* lane_j
     }
 }
 
+// LT levels (the live-edge form of the linear-threshold model): every
+// frontier colour at vertex v follows v's kept in-edge for its sample, one
+// Philox draw per (sample, vertex) against the row's weight prefix (binary
+// search for the first edge whose prefix passes the draw); the source gets the
+// colour.  Each colour has at most one frontier vertex (its walk), so one
+// thread per frontier unit is enough.
+template <bool ro>
+__device__ __forceinline__ void expand_lt(const Eng& E, const uint32_t* lane_j, const PhiloxKeys& K, uint64_t U,
+                                          uint64_t& n_edges, uint64_t& n_calls) {
+    const uint32_t f_lo = (uint32_t)E.first_id, f_hi = (uint32_t)(E.first_id >> 32);
+    for (uint64_t u = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; u < U;
+         u += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t occ = LD<ro>(&E.list_occ[u]);
+        const uint32_t mrow = LD<ro>(&E.list_mrow[u]);
+        const uint32_t v = LD<ro>(&E.list_v[u]);
+        const uint64_t rs = LD<ro>(&E.list_rs[u]), re = LD<ro>(&E.list_re[u]);
+        const uint64_t base = __ldg(&E.wpre[rs]);
+        const uint64_t total = __ldg(&E.wpre[re]) - base;
+        uint64_t words = occ;
+        while (words) {
+            const uint32_t i = __ffsll((long long)words) - 1;
+            words &= words - 1;
+            uint64_t x = LD<ro>(&E.stage[(uint64_t)mrow * E.WB + i]);
+            while (x) {
+                const uint32_t c = __ffsll((long long)x) - 1;
+                x &= x - 1;
+                const uint32_t j = lane_j[(i << 6) + c];
+                const uint32_t slo = f_lo + j;
+                const uint32_t shi = f_hi + (slo < j ? 1u : 0u);
+                const uint4 rnd = philox4x32_10(make_uint4(slo, shi, v, 0x40000000u), K);
+                ++n_calls;
+                const uint64_t r = rnd.x;
+                if (r >= total) continue;  // v keeps no in-edge for this sample
+                const uint64_t key = base + r;
+                uint64_t lo = rs, hi = re - 1;  // first e with wpre[e + 1] > key
+                while (lo < hi) {
+                    const uint64_t mid = (lo + hi) >> 1;
+                    if (__ldg(&E.wpre[mid + 1]) > key) hi = mid; else lo = mid + 1;
+                }
+                ++n_edges;
+                or_next(E, __ldg(&E.col[lo]), i, 1ull << c);
+            }
+        }
+    }
+}
+
 // The expand phase.  part selects which directions this instance runs (the
 // per-level kernels split them so that the plain push kernel carries no
 // register of the others): kPartPush, kPartAlt (filtered push and pull) or
@@ -478,7 +524,7 @@ __device__ void dev_expand(const Eng& E, uint32_t* lane_j) {
     const uint32_t dir = L2(&ctl->dir);
     const bool pull = dir == kDirPull && E.frontd;
     if (part == kPartPush && dir != kDirPush) return;
-    if (part == kPartAlt && dir == kDirPush) return;
+    if (part == kPartAlt && (dir == kDirPush || E.model == FBPT_MODEL_LT)) return;
     if (G == 0) return;
     const uint64_t U = L2(&ctl->list_count);
     const uint64_t nchunks = (G + kChunk - 1) / kChunk;
@@ -490,7 +536,8 @@ __device__ void dev_expand(const Eng& E, uint32_t* lane_j) {
     const uint32_t lane = lane_id();
     const PhiloxKeys K = philox_keys(E.seed);
     uint64_t n_edges = 0, n_calls = 0;
-    if (part != kPartPush && pull) dev_pull(E, lane_j, K, n_edges, n_calls);
+    if (E.model == FBPT_MODEL_LT) expand_lt<part != kPartAll>(E, lane_j, K, U, n_edges, n_calls);
+    else if (part != kPartPush && pull) dev_pull(E, lane_j, K, n_edges, n_calls);
     else if (part != kPartPush && dir == kDirFiltered)
         expand_push<true, part != kPartAll>(E, lane_j, K, G, U, nchunks, n_edges, n_calls);
     else if (part != kPartAlt)
@@ -1513,6 +1560,13 @@ int run_setup(Run& r, fbpt_graph* g, uint64_t seed, uint64_t first_id, uint64_t 
     const uint32_t WB = force_wb ? force_wb : (uint32_t)std::min<uint64_t>(W * B, (S + 63) / 64);
     if (WB > kMaxWords) return fail(FBPT_EINVAL, "fbpt_sample: row width above 64 words");
     if (o.schedule > FBPT_SCHED_FILTERED) return fail(FBPT_EINVAL, "fbpt_sample: bad schedule");
+    if (o.model != FBPT_MODEL_IC && o.model != FBPT_MODEL_LT) return fail(FBPT_EINVAL, "fbpt_sample: bad model");
+    if (o.model == FBPT_MODEL_LT) {
+        // LT levels are push only: a choice among other directions does not apply
+        if (o.schedule == FBPT_SCHED_PULL || o.schedule == FBPT_SCHED_FILTERED || o.unfused)
+            return fail(FBPT_EUNSUPPORTED, "fbpt_sample: the LT model runs fused push levels only");
+        o.schedule = FBPT_SCHED_PUSH;
+    }
     // pull levels need dense frontier rows (WB <= 8 words), fused units and 32-bit edge ids
     const bool pull_ok = WB <= kPullMaxWords && !o.unfused && g->m < (1ull << 32);
     if (o.schedule == FBPT_SCHED_PULL && !pull_ok)
@@ -1537,6 +1591,7 @@ int run_setup(Run& r, fbpt_graph* g, uint64_t seed, uint64_t first_id, uint64_t 
     r.out = out;
 
     if (r.dense) FBPT_TRY(ensure_out_csr(g, r.st));
+    if (o.model == FBPT_MODEL_LT) FBPT_TRY(ensure_lt_weights(g, r.st));
     FBPT_TRY(ws_get(g, WB, o.unfused != 0, r.dense, r.st, &r.ws));
     // per-lane segments sized to hold about twice the expected RR set, so that
     // few lanes fall back to the shared spill log (which the sweep compacts
@@ -1607,6 +1662,8 @@ int run_arm(Run& r) {
     E.frontd = ws->frontd; E.fstamp = ws->fstamp;
     E.policy = (r.o.schedule == FBPT_SCHED_LEARNED && r.o.policy) ? r.o.policy->d_params : nullptr;
     E.alt = r.o.schedule == FBPT_SCHED_PUSH ? 0u : 1u;
+    E.model = r.o.model;
+    E.wpre = g->wpre;
     E.m = g->m;
     E.pend_cap = ws->pend_cap; E.list_cap = ws->list_cap; E.chunk_cap = ws->chunk_cap;
     E.spill_cap = ws->spill_cap;

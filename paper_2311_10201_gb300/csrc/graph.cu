@@ -41,7 +41,57 @@ __global__ void k_outfill(const uint64_t* row_ptr, const uint32_t* col, uint32_t
         }
 }
 
+// LT weights in units of 2^-32 (0xFFFFFFFF is the always-kept marker: 2^32).
+__global__ void k_lt_weights(const uint32_t* thr, uint64_t m, uint64_t* w) {
+    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (uint64_t)gridDim.x * blockDim.x)
+        w[e] = thr[e] == 0xFFFFFFFFu ? (1ull << 32) : (uint64_t)thr[e];
+}
+
+__global__ void k_lt_rows(const uint64_t* row_ptr, const uint64_t* wpre, uint32_t n, unsigned* bad) {
+    for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (uint64_t)gridDim.x * blockDim.x)
+        if (wpre[row_ptr[v + 1]] - wpre[row_ptr[v]] > (1ull << 32)) atomicOr(bad, 1u);
+}
+
 }  // namespace
+
+int ensure_lt_weights(fbpt_graph* g, cudaStream_t st) {
+    if (g->lt_rows < 0) return fail(FBPT_EINVAL, "LT model: some row's in-edge weights sum to more than 1");
+    if (g->wpre) return FBPT_OK;
+    uint64_t* w = nullptr;
+    unsigned* bad = nullptr;
+    unsigned hbad = 0;
+    FBPT_CUDA_TRY(cudaMalloc(&g->wpre, sizeof(uint64_t) * (g->m + 1)));
+    int rc = FBPT_OK;
+    if (cudaMallocAsync(&w, sizeof(uint64_t) * std::max<uint64_t>(g->m, 1), st) != cudaSuccess ||
+        cudaMallocAsync(&bad, sizeof(unsigned), st) != cudaSuccess)
+        rc = fail(FBPT_ENOMEM, "LT model: weight prefix scratch");
+    if (rc == FBPT_OK) {
+        const int sms = device_sm_count();
+        k_lt_weights<<<sms * 8, 256, 0, st>>>(g->thr, g->m, w);
+        rc = exclusive_scan_u64(w, g->wpre, g->m, st);
+    }
+    if (rc == FBPT_OK) {
+        cudaMemsetAsync(bad, 0, sizeof(unsigned), st);
+        k_lt_rows<<<device_sm_count() * 8, 256, 0, st>>>(g->row_ptr, g->wpre, g->n, bad);
+        if (cudaMemcpyAsync(&hbad, bad, sizeof(unsigned), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            rc = fail(FBPT_ECUDA, "LT model: weight check failed");
+    }
+    if (w) cudaFreeAsync(w, st);
+    if (bad) cudaFreeAsync(bad, st);
+    if (rc == FBPT_OK && hbad) {
+        g->lt_rows = -1;
+        rc = fail(FBPT_EINVAL, "LT model: some row's in-edge weights sum to more than 1");
+    }
+    if (rc != FBPT_OK) {
+        cudaStreamSynchronize(st);
+        cudaFree(g->wpre);
+        g->wpre = nullptr;
+        return rc;
+    }
+    g->lt_rows = 1;
+    return FBPT_OK;
+}
 
 int ensure_out_csr(fbpt_graph* g, cudaStream_t st) {
     if (g->orow) return FBPT_OK;
@@ -138,6 +188,7 @@ extern "C" int fbpt_graph_destroy(fbpt_graph* g) {
     cudaFree(g->orow);
     cudaFree(g->odst);
     cudaFree(g->oeid);
+    cudaFree(g->wpre);
     cudaFree(g->row_ptr);
     cudaFree(g->col);
     cudaFree(g->thr);

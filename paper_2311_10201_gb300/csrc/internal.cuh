@@ -148,6 +148,8 @@ struct Eng {
     uint64_t* frontd;
     uint32_t* fstamp;
     const float* policy;          // kPolicyParams weights of the schedule network, or NULL
+    const uint64_t* wpre;         // LT: exclusive prefix of the edge weights (m + 1)
+    uint32_t model;               // fbpt_model
     uint64_t m;
     uint64_t pend_cap, list_cap, chunk_cap, spill_cap;
     uint32_t unfused;
@@ -187,6 +189,8 @@ struct fbpt_graph {
     uint64_t* orow = nullptr;     // n + 1
     uint32_t* odst = nullptr;     // m
     uint32_t* oeid = nullptr;     // m (edge ids < 2^32)
+    uint64_t* wpre = nullptr;     // m + 1: exclusive prefix of the LT weights (units of 2^-32), built on first use
+    int lt_rows = 0;              // 1: every row's LT weights sum to at most 1; -1: some row's exceed it
     fbpt::Workspace* ws = nullptr;
     double rr_hint = 32.0;        // running estimate of RR entries per sample
     fbpt_tuning tuned = {};       // launch shape measured by fbpt_autotune
@@ -205,6 +209,8 @@ int imm_impl(fbpt_graph* g, uint32_t k, double epsilon, double ell, uint64_t see
              fbpt_stats* stats);
 // Builds g's out-edge CSR if it is not there yet (FBPT_EUNSUPPORTED for m >= 2^32).
 int ensure_out_csr(fbpt_graph* g, cudaStream_t st);
+// Builds g's LT weight prefix if it is not there yet; FBPT_EINVAL if a row's weights exceed 1.
+int ensure_lt_weights(fbpt_graph* g, cudaStream_t st);
 // Device-wide exclusive scan of n counts into n+1 uint64 offsets (out[n] = total).
 int exclusive_scan_u32(const uint32_t* in, uint64_t* out, uint64_t n, cudaStream_t st);
 int exclusive_scan_u64(const uint64_t* in, uint64_t* out, uint64_t n, cudaStream_t st);
