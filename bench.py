@@ -93,6 +93,22 @@ def build_workload(name=WORKLOAD):
     return w, w.graphs[0]
 
 
+def rank_samples(rank: int, S: int):
+    """Sample ids of one rank under weak scaling: every rank samples S ids of
+    its own range on a replica of the graph (no data-path collective)."""
+    return rank * S, S
+
+
+def max_over_ranks(dist, value: float, device: str) -> float:
+    """The step time of the whole job: the slowest rank's."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def cpu_baseline(g, seed, sample_count):
     """The oracle as it stands (per-sample BFS + greedy), all host cores."""
     import oracle
@@ -204,7 +220,7 @@ def main():
     S = args.samples
     k = w.k or 100
     seed = w.seeds[0]
-    first = rank * S
+    first, S = rank_samples(rank, S)
     stream = torch.cuda.current_stream()
     dg = fbpt.Graph.from_synth(g, stream)
     # launch shape: measured by the autotuner before the timed region (like a
@@ -243,9 +259,7 @@ def main():
     ms = ev0.elapsed_time(ev1)
     clk = clocks.stop()
     if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(dist, ms, "cuda")
         dist.barrier()
     ms_step = ms / args.steps
     value = S * world * args.steps / (ms / 1e3)
@@ -345,9 +359,7 @@ def main():
         torch.cuda.synchronize()
         e2e_s = (time.perf_counter() - t0) / e2e_steps
         if dist:
-            t = torch.tensor([e2e_s], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
+            e2e_s = max_over_ranks(dist, e2e_s, "cuda")
         e2e = {"value": S * world / e2e_s, "unit": "RR samples/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
 
