@@ -101,6 +101,23 @@ struct Smem {
     uint32_t last, abort, nstill, dir;
 };
 
+// dst[0 .. count) = src[0 .. count) (count <= kMaxLanes + 1), all loads of a
+// thread issued before any store so that they are in flight together.
+__device__ __forceinline__ void fill_smem(uint32_t* dst, const uint32_t* src, uint32_t count) {
+    constexpr uint32_t kPer = (kMaxLanes + 1 + kThreads - 1) / kThreads;
+    uint32_t v[kPer];
+#pragma unroll
+    for (uint32_t k = 0; k < kPer; ++k) {
+        const uint32_t i = threadIdx.x + k * kThreads;
+        v[k] = i < count ? L2(&src[i]) : 0u;
+    }
+#pragma unroll
+    for (uint32_t k = 0; k < kPer; ++k) {
+        const uint32_t i = threadIdx.x + k * kThreads;
+        if (i < count) dst[i] = v[k];
+    }
+}
+
 __device__ __forceinline__ void phase_begin(Ctl* ctl, int p) {
     if (threadIdx.x == 0) atomicMin(&ctl->ph_t0[p], globaltimer_ns());
 }
@@ -160,7 +177,7 @@ __device__ void dev_sweep(const Eng& E, Smem& sm) {
     }
     phase_begin(ctl, 2);
     __syncthreads();
-    for (uint32_t k = threadIdx.x; k <= F; k += blockDim.x) sm.lane[k] = L2(&ctl->fin_pre[k]);
+    fill_smem(sm.lane, ctl->fin_pre, F + 1);
     for (uint32_t i = threadIdx.x; i < E.WB; i += blockDim.x) sm.fin[i] = L2(&ctl->fin_mask[i]);
     __syncthreads();
     const uint32_t total = sm.lane[F];
@@ -531,7 +548,7 @@ __device__ void dev_expand(const Eng& E, uint32_t* lane_j) {
     if (nchunks > E.chunk_cap || U > E.list_cap) return;  // overflow already flagged by commit
     phase_begin(ctl, 0);
     __syncthreads();
-    for (uint32_t l = threadIdx.x; l < 64u * E.WB; l += blockDim.x) lane_j[l] = L2(&ctl->lane_j[l]);
+    fill_smem(lane_j, ctl->lane_j, 64u * E.WB);
     __syncthreads();
     const uint32_t lane = lane_id();
     const PhiloxKeys K = philox_keys(E.seed);
