@@ -361,7 +361,8 @@ int fbpt_policy_loss_grad(const float* params, const float* features, const uint
 int fbpt_edge_draws(uint64_t seed, const uint64_t* s, const uint64_t* e, uint64_t count, uint32_t* out);
 int fbpt_start_vertices(uint64_t seed, const uint64_t* s, uint64_t count, uint32_t n, uint32_t* out);
 
-/* sizeof(fbpt_opts), sizeof(fbpt_rrsets), sizeof(fbpt_stats) into sizes[0..2]
+/* sizeof(fbpt_opts), sizeof(fbpt_rrsets), sizeof(fbpt_stats), sizeof(fbpt_tuning),
+ * sizeof(fbpt_imm_result), sizeof(fbpt_trace_row) into sizes[0 .. min(count, 6) - 1]
  * (count >= 3), so that bindings can check their struct layouts. */
 int fbpt_abi_sizes(uint64_t* sizes, int count);
 

@@ -40,7 +40,7 @@ class Opts(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("words", ctypes.c_uint32), ("slots", ctypes.c_uint32), ("refill", ctypes.c_uint32),
-                ("blocks", ctypes.c_uint32), ("model", ctypes.c_uint32), ("candidates", ctypes.c_uint32), ("schedule", ctypes.c_uint32),
+                ("blocks", ctypes.c_uint32), ("candidates", ctypes.c_uint32), ("schedule", ctypes.c_uint32),
                 ("probe_samples", ctypes.c_uint64), ("probe_rate", ctypes.c_double),
                 ("rr_per_sample", ctypes.c_double)]
 
@@ -145,9 +145,10 @@ def lib():
             f = getattr(L, name)
             f.restype = res
             f.argtypes = args
-        sizes = (ctypes.c_uint64 * 3)()
-        L.fbpt_abi_sizes(sizes, 3)
-        want = [ctypes.sizeof(Opts), ctypes.sizeof(RRSetsC), ctypes.sizeof(Stats)]
+        sizes = (ctypes.c_uint64 * 6)()
+        L.fbpt_abi_sizes(sizes, 6)
+        want = [ctypes.sizeof(Opts), ctypes.sizeof(RRSetsC), ctypes.sizeof(Stats), ctypes.sizeof(Tuning),
+                ctypes.sizeof(ImmResult), TRACE_DTYPE.itemsize]
         if list(sizes) != want:
             raise RuntimeError(f"libfbpt struct layout mismatch: library {list(sizes)} vs binding {want}")
         _lib = L

@@ -47,10 +47,10 @@ extern "C" const char* fbpt_last_error(void) { return last_error(); }
 extern "C" int fbpt_version(void) { return FBPT_VERSION; }
 
 extern "C" int fbpt_abi_sizes(uint64_t* sizes, int count) {
-    if (!sizes || count < 3) return fail(FBPT_EINVAL, "fbpt_abi_sizes: need 3 entries");
-    sizes[0] = sizeof(fbpt_opts);
-    sizes[1] = sizeof(fbpt_rrsets);
-    sizes[2] = sizeof(fbpt_stats);
+    if (!sizes || count < 3) return fail(FBPT_EINVAL, "fbpt_abi_sizes: need at least 3 entries");
+    const uint64_t all[6] = {sizeof(fbpt_opts), sizeof(fbpt_rrsets), sizeof(fbpt_stats), sizeof(fbpt_tuning),
+                             sizeof(fbpt_imm_result), sizeof(fbpt_trace_row)};
+    for (int i = 0; i < count && i < 6; ++i) sizes[i] = all[i];
     return FBPT_OK;
 }
 

@@ -42,6 +42,10 @@ def test_struct_layouts_match(lib):
     sizes = (ctypes.c_uint64 * 3)()
     assert lib.fbpt_abi_sizes(sizes, 3) == 0
     assert list(sizes) == [ctypes.sizeof(fbpt.Opts), ctypes.sizeof(fbpt.RRSetsC), ctypes.sizeof(fbpt.Stats)]
+    all6 = (ctypes.c_uint64 * 6)()
+    assert lib.fbpt_abi_sizes(all6, 6) == 0
+    assert list(all6) == [ctypes.sizeof(fbpt.Opts), ctypes.sizeof(fbpt.RRSetsC), ctypes.sizeof(fbpt.Stats),
+                          ctypes.sizeof(fbpt.Tuning), ctypes.sizeof(fbpt.ImmResult), fbpt.TRACE_DTYPE.itemsize]
     assert lib.fbpt_version() == 1
 
 
