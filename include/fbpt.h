@@ -240,8 +240,9 @@ typedef struct fbpt_tuning {
  * it keeps the fastest width and the fewest CTAs within 3% of its rate.  base supplies the schedule and policy
  * (NULL = push); when base->words is set, base->words * base->slots (slots 0
  * read as 1) caps the widths tried.  A learned (or heuristic) schedule is then
- * judged at that shape against the heuristic (or learned, with a policy) and
- * plain push: another schedule is kept only if it is at least 3% faster.  The result is stored on g (used by fbpt_sample_batched) and
+ * judged at that shape against the heuristic (or learned, with a policy): the
+ * other is kept only if it is at least 3% faster; plain push (no second
+ * expand kernel per level) is kept whenever it is within 3% of the best.  The result is stored on g (used by fbpt_sample_batched) and
  * copied to out (may be NULL).  Output bits never depend on the shape. */
 int fbpt_autotune(fbpt_graph* g, uint64_t seed, uint64_t S, const fbpt_opts* base, fbpt_tuning* out);
 /* The shape stored on g by fbpt_autotune; FBPT_EINVAL if it was never tuned. */

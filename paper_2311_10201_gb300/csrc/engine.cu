@@ -604,10 +604,11 @@ __device__ __forceinline__ uint32_t nth_bit64(uint64_t m, uint32_t r) {
 __device__ void dev_commit(const Eng& E, Smem& sm) {
     Ctl* ctl = E.ctl;
     const uint32_t P = (uint32_t)min((uint64_t)L2(&ctl->pend_count), E.pend_cap);
-    // vertices per warp: spread a small level over every warp of the grid (the
-    // work is a chain of dependent loads per vertex), up to one per lane
+    // vertices per warp: spread a small level over more warps of the grid (the
+    // work is a chain of dependent loads per vertex), but at least 8 per warp so
+    // that each warp's fixed bookkeeping stays amortised; up to one per lane
     const uint64_t nwarp = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    const uint32_t vpw = (uint32_t)min((uint64_t)32, max((uint64_t)1, (P + nwarp - 1) / nwarp));
+    const uint32_t vpw = (uint32_t)min((uint64_t)32, max((uint64_t)8, (P + nwarp - 1) / nwarp));
     if ((uint64_t)blockIdx.x * (blockDim.x >> 5) * vpw >= P) return;  // no pending vertex for this CTA
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < 2 * E.WB; i += blockDim.x) sm.act[i] = 0;
@@ -2112,17 +2113,23 @@ int autotune_impl(fbpt_graph* g, uint64_t seed, uint64_t S, const fbpt_opts* bas
     // faster at the chosen shape
     uint32_t best_sched = o.schedule;
     if (o.schedule == FBPT_SCHED_LEARNED || o.schedule == FBPT_SCHED_HEURISTIC) {
-        const uint32_t others[2] = {o.schedule == FBPT_SCHED_LEARNED ? (uint32_t)FBPT_SCHED_HEURISTIC
-                                                                    : (uint32_t)FBPT_SCHED_LEARNED,
-                                    (uint32_t)FBPT_SCHED_PUSH};
-        for (uint32_t k = 0; k < 2; ++k) {
-            if (others[k] == FBPT_SCHED_LEARNED && !o.policy) continue;
+        const uint32_t other = o.schedule == FBPT_SCHED_LEARNED ? (uint32_t)FBPT_SCHED_HEURISTIC
+                                                                : (uint32_t)FBPT_SCHED_LEARNED;
+        if (other != FBPT_SCHED_LEARNED || o.policy) {
             double rate = 0;
-            FBPT_TRY(probe(best_wb, best_blocks, rate, others[k]));
+            FBPT_TRY(probe(best_wb, best_blocks, rate, other));
             if (rate > 1.03 * best_rate) {
                 best_rate = rate;
-                best_sched = others[k];
+                best_sched = other;
             }
+        }
+        // plain push (no second expand kernel per level) is kept whenever it is
+        // within 3% of the best
+        double rate = 0;
+        FBPT_TRY(probe(best_wb, best_blocks, rate, FBPT_SCHED_PUSH));
+        if (rate >= 0.97 * best_rate) {
+            best_rate = std::max(best_rate, rate);
+            best_sched = FBPT_SCHED_PUSH;
         }
     }
     t.words = std::min<uint32_t>(best_wb, 8);
