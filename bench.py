@@ -35,7 +35,7 @@ WORKLOAD = "rmat_s22_wc"
 # at 64-word rows: 55,187,712 B read + 230,400 B written for 1,496,061 groups).
 # The bench scales it by its own groups per launch; None once the kernel has
 # changed since that capture.
-EXPAND_DRAM_BYTES_PER_GROUP = (55187712 + 230400) / 1496061
+EXPAND_DRAM_BYTES_PER_GROUP = (55207680 + 223744) / 1496061
 METRIC = "RR samples/s (bit-exact RR sets + greedy seeds, R-MAT s22 WC, 1,048,576 samples, k=100)"
 
 
