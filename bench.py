@@ -368,9 +368,9 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(g, seed, 8192)
 
-    # kernels per step: 5 or 6 per level, the final sweep, the row-length scan (3), the
+    # kernels per step: 4 or 5 per level, the final sweep, the row-length scan (3), the
     # three row-ordering kernels, greedy 2 per pick + 3
-    per_level = 5 + (1 if kw.get("schedule", "push") != "push" else 0)  # + the filtered/pull expand
+    per_level = 4 + (1 if kw.get("schedule", "push") != "push" else 0)  # + the filtered/pull expand
     launches_step = per_level * int(st.levels) + 1 + 3 + 3 + 2 * k + 3
     if rank == 0:
         print(json.dumps({

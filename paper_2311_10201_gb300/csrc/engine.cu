@@ -17,13 +17,15 @@
 //
 // One level ("tick") has five phases:
 //   sweep    finished lanes: RR pairs out, bits cleared, spill log compacted
-//   init     start vertices of lanes assigned a new sample
 //   expand   frontier units x 4-edge groups -> next rows, pending vertices
 //   commit   pending vertices -> visited, new frontier list, lane entry lists
 //   schedule (one CTA) finished lanes, refills, loop condition
-// They run as five kernels per level (host loop or CUDA-graph WHILE loop) or
-// inside one persistent cooperative kernel, where sweep, init and expand of
-// a level share a phase and bounded grid barriers separate the phases.
+//   init     start vertices of lanes assigned a new sample
+// They run as four kernels per level (host loop or CUDA-graph WHILE loop, where
+// the sweep is a branch beside the expand; the scheduler CTA also places the
+// start vertices) or inside one persistent cooperative kernel, where sweep,
+// init and expand of a level share a phase and bounded grid barriers separate
+// the phases.
 //
 // Liveness never reads visited[]: the expand draws for every colour of the
 // frontier mask and the commit removes colours a vertex has already seen.
@@ -96,7 +98,7 @@ struct Smem {
     // per word, block-scan scratch
     SchedHead h;
     unsigned long long still[kMaxWords], sfin[kMaxWords], init[kMaxWords];
-    unsigned long long bscan[kThreads / 32 + 1];
+    unsigned long long mscan[33][6];  // schedule: block-scan scratch (32 warps + totals)
     float feat[8], h1[kPolicyHidden], h2[kPolicyHidden], out[kPolicyOut];
     uint32_t last, abort, nstill, dir;
 };
@@ -164,7 +166,9 @@ __device__ __forceinline__ void sweep_entry(const Eng& E, const uint64_t* fin, u
     atomicAdd(&E.vcount[v], (uint32_t)__popcll(m));
 }
 
-__device__ void dev_sweep(const Eng& E, Smem& sm) {
+// pre: shared memory for the finished lanes' entry prefixes (kMaxLanes + 1);
+// fin: shared memory for the finished-lane masks (kMaxWords).
+__device__ void dev_sweep(const Eng& E, uint32_t* pre, uint64_t* fin) {
     Ctl* ctl = E.ctl;
     const uint32_t F = L2(&ctl->fin_count);
     const uint32_t spill = L2(&ctl->spill_sweep);
@@ -177,10 +181,10 @@ __device__ void dev_sweep(const Eng& E, Smem& sm) {
     }
     phase_begin(ctl, 2);
     __syncthreads();
-    fill_smem(sm.lane, ctl->fin_pre, F + 1);
-    for (uint32_t i = threadIdx.x; i < E.WB; i += blockDim.x) sm.fin[i] = L2(&ctl->fin_mask[i]);
+    fill_smem(pre, ctl->fin_pre, F + 1);
+    for (uint32_t i = threadIdx.x; i < E.WB; i += blockDim.x) fin[i] = L2(&ctl->fin_mask[i]);
     __syncthreads();
-    const uint32_t total = sm.lane[F];
+    const uint32_t total = pre[F];
     const uint32_t lane = lane_id();
     const uint64_t wid = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarp = ((uint64_t)gridDim.x * blockDim.x) >> 5;
@@ -191,14 +195,14 @@ __device__ void dev_sweep(const Eng& E, Smem& sm) {
             uint32_t lo = 0, hi = F;  // largest k < F with prefix[k] <= idx
             while (hi - lo > 1) {
                 const uint32_t mid = (lo + hi) >> 1;
-                if (sm.lane[mid] <= idx) lo = mid; else hi = mid;
+                if (pre[mid] <= idx) lo = mid; else hi = mid;
             }
             const uint32_t l = L2(&ctl->fin_lane[lo]);
-            const uint32_t p = idx - sm.lane[lo];
+            const uint32_t p = idx - pre[lo];
             const uint32_t v = L2(&E.seg[(uint64_t)l * E.seg_cap + p]);
             const uint64_t dst = L2(&ctl->lane_base[l]) + p;
             if (dst < cap) E.rows_v[dst] = v;
-            sweep_entry(E, sm.fin, l, v);
+            sweep_entry(E, fin, l, v);
         }
     }
     if (spill) {
@@ -216,13 +220,13 @@ __device__ void dev_sweep(const Eng& E, Smem& sm) {
                 l = (uint32_t)(ent >> (2 * kSpillPosBits));
                 p = (ent >> kSpillPosBits) & kSpillMask;
                 v = (uint32_t)(ent & kSpillMask);
-                done = (sm.fin[l >> 6] >> (l & 63)) & 1ull;
+                done = (fin[l >> 6] >> (l & 63)) & 1ull;
             }
             const uint64_t kp = warp_alloc<unsigned long long>(&ctl->spill_len[dst], (ok && !done) ? 1ull : 0ull);
             if (ok && done) {
                 const uint64_t d = L2(&ctl->lane_base[l]) + p;
                 if (d < cap) E.rows_v[d] = v;
-                sweep_entry(E, sm.fin, l, v);
+                sweep_entry(E, fin, l, v);
             } else if (ok) {
                 if (kp < E.spill_cap) E.spill[(uint64_t)dst * E.spill_cap + kp] = ent;
                 else atomicOr(&ctl->error, (unsigned)kErrSpillOverflow);
@@ -844,26 +848,41 @@ __device__ void policy_forward(const float* P, Smem& sm) {
     __syncthreads();
 }
 
-// ---- schedule (one CTA of kThreads threads) ---------------------------------------------
+// ---- schedule (one CTA) ---------------------------------------------------------------
 
-// Exclusive prefix over the CTA's threads (all must call); total gets the sum.
-__device__ __forceinline__ unsigned long long block_excl_scan(unsigned long long v, unsigned long long* scratch,
-                                                              unsigned long long& total) {
+constexpr uint32_t kSchedThreads = 1024;  // threads of the per-level scheduler CTA
+constexpr uint32_t kScanVals = 6;
+
+// Exclusive prefixes of kScanVals values over the CTA's threads in one pass (all
+// threads call): v[c] becomes its prefix, tot[c] the sum.  scratch has 33 rows.
+__device__ __forceinline__ void block_scan_multi(unsigned long long (&v)[kScanVals],
+                                                 unsigned long long (*scratch)[kScanVals],
+                                                 unsigned long long (&tot)[kScanVals]) {
     const uint32_t lane = lane_id(), warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const unsigned long long incl = warp_incl_scan(v);
-    if (lane == 31) scratch[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-        const unsigned long long x = lane < nw ? scratch[lane] : 0ull;
-        const unsigned long long xi = warp_incl_scan(x);
-        if (lane < nw) scratch[lane] = xi - x;
-        if (lane == nw - 1) scratch[kThreads / 32] = xi;
+    unsigned long long incl[kScanVals];
+#pragma unroll
+    for (uint32_t c = 0; c < kScanVals; ++c) incl[c] = warp_incl_scan(v[c]);
+    if (lane == 31) {
+#pragma unroll
+        for (uint32_t c = 0; c < kScanVals; ++c) scratch[warp][c] = incl[c];
     }
     __syncthreads();
-    total = scratch[kThreads / 32];
-    const unsigned long long r = scratch[warp] + incl - v;
+    if (warp == 0) {
+#pragma unroll
+        for (uint32_t c = 0; c < kScanVals; ++c) {
+            const unsigned long long x = lane < nw ? scratch[lane][c] : 0ull;
+            const unsigned long long xi = warp_incl_scan(x);
+            if (lane < nw) scratch[lane][c] = xi - x;
+            if (lane == 31) scratch[32][c] = xi;
+        }
+    }
     __syncthreads();
-    return r;
+#pragma unroll
+    for (uint32_t c = 0; c < kScanVals; ++c) {
+        tot[c] = scratch[32][c];
+        v[c] = scratch[warp][c] + incl[c] - v[c];
+    }
+    __syncthreads();
 }
 
 // Lanes that held a sample but are absent from the new frontier have finished
@@ -871,13 +890,19 @@ __device__ __forceinline__ unsigned long long block_excl_scan(unsigned long long
 // (lane refill) or once no lane is still traversing (batch mode).  The new
 // frontier list becomes the expand's input; the loop continues while any
 // lane holds a sample.  Every thread owns a run of consecutive lanes (inside
-// one word), so lane-order prefixes are block scans.
+// one word; at most kPer of them), so lane-order prefixes are block scans.
+// With init, the CTA also places the start vertex of every lane given a
+// sample (one lane per thread); otherwise dev_init does it from init_w.
+template <uint32_t kPer, bool init>
 __device__ void dev_schedule(const Eng& E, Smem& sm) {
     Ctl* ctl = E.ctl;
     const uint32_t t = threadIdx.x;
     const uint32_t WB = E.WB, L = 64u * WB;
     SchedHead& h = sm.h;
-    // 1. the control fields this step reads, one load per thread
+    // 1. everything the step reads, in one round of loads: the control fields,
+    // the lane masks of each word and the counts and sample ids of this
+    // thread's lanes.  per: the smallest power of two with per * blockDim >= L
+    // (per <= kPer by the launch shape), so that a run never straddles two words.
     switch (t) {
         case 0: h.err = L2(&ctl->error); break;
         case 1: h.next_j = L2(&ctl->next_j); break;
@@ -899,88 +924,114 @@ __device__ void dev_schedule(const Eng& E, Smem& sm) {
         case 19: case 20: case 21: h.ph_t1[t - 19] = L2(&ctl->ph_t1[t - 19]); break;
         default: break;
     }
-    if (t < WB) {
-        const unsigned long long run = L2(&ctl->run_w[t]), act = L2(&ctl->act_w[t]);
-        sm.still[t] = run & act;
-        sm.sfin[t] = run & ~act;
-        sm.init[t] = 0;
-    }
-    __syncthreads();
-    // lanes per thread: the smallest power of two with per * blockDim >= L,
-    // so that a run never straddles two words (per <= 16 for L <= 4096)
     uint32_t per = 1;
     while (per * blockDim.x < L) per <<= 1;
     const uint32_t a0 = min(t * per, L), a1 = min(a0 + per, L);
     const uint32_t wi = a0 >> 6;
-    const unsigned long long runmask = per >= 64 ? ~0ull : ((1ull << per) - 1ull);
-    const unsigned long long myfin = a0 < a1 ? (sm.sfin[wi] >> (a0 & 63)) & runmask : 0ull;
-    const unsigned long long mystill = a0 < a1 ? (sm.still[wi] >> (a0 & 63)) & runmask : 0ull;
-    // 2. finished lanes: their count and row lengths in lane order
-    unsigned long long rsum = 0;
-    for (unsigned long long f = myfin; f; f &= f - 1)
-        rsum += L2(&ctl->lane_cnt[a0 + __ffsll((long long)f) - 1]);
-    unsigned long long F64 = 0, R64 = 0, S64 = 0, N64 = 0, ST64 = 0;
-    const unsigned long long k0 = block_excl_scan((unsigned long long)__popcll(myfin), sm.bscan, F64);
-    const unsigned long long rb0 = block_excl_scan(rsum, sm.bscan, R64);
-    const uint32_t F = (uint32_t)F64;
-    // 3. each finished lane's row: staging range, sample index, entry of the fin list
-    bool spilled = false;
-    unsigned long long segsum = 0;
-    {
-        unsigned long long rb = h.pair_cursor + rb0;
-        uint32_t k = (uint32_t)k0;
-        for (unsigned long long f = myfin; f; f &= f - 1) {
-            const uint32_t l = a0 + __ffsll((long long)f) - 1;
-            const uint32_t rc = L2(&ctl->lane_cnt[l]);
-            const uint32_t j = L2(&ctl->lane_j[l]);
-            ctl->retired_j[l] = j;
-            ctl->lane_base[l] = rb;
-            E.row_start[j] = rb;
-            E.row_len[j] = rc;
-            rb += rc;
-            ctl->lane_cnt[l] = 0;
-            ctl->fin_lane[k] = l;
-            const uint32_t sg = min(rc, E.seg_cap);
-            sm.lane[k] = sg;
-            segsum += sg;
-            spilled |= rc > E.seg_cap;
-            ++k;
+    unsigned long long run = 0, act = 0;
+    if (a0 < a1) {
+        run = L2(&ctl->run_w[wi]);
+        act = L2(&ctl->act_w[wi]);
+    }
+    uint32_t cnt[kPer], jj[kPer];
+#pragma unroll
+    for (uint32_t c = 0; c < kPer; ++c) {
+        const bool in = a0 + c < a1;
+        cnt[c] = in ? L2(&ctl->lane_cnt[a0 + c]) : 0u;
+        jj[c] = in ? L2(&ctl->lane_j[a0 + c]) : 0u;
+    }
+    if (t < WB) sm.init[t] = 0;
+    if (a0 < a1 && (a0 & 63) == 0) {  // the first thread of each word keeps its masks
+        sm.still[wi] = run & act;
+        sm.sfin[wi] = run & ~act;
+    }
+    const unsigned long long runmask = a0 < a1 ? ((per >= 64 ? ~0ull : ((1ull << per) - 1ull))) : 0ull;
+    const unsigned long long myfin = ((run & ~act) >> (a0 & 63)) & runmask;
+    const unsigned long long mystill = ((run & act) >> (a0 & 63)) & runmask;
+    const unsigned long long freem = ~mystill & runmask;
+    __syncthreads();
+    // the commit has consumed the pending list: the init below starts the next one
+    if (init && t == 0) ctl->pend_count = 0;
+    // 2. per thread: finished lanes, their entries, segment entries, spilled
+    // lanes; free and traversing lanes.  One scan gives every prefix.
+    unsigned long long sv[kScanVals] = {(unsigned long long)__popcll(myfin), 0ull, 0ull,
+                                        (unsigned long long)__popcll(freem), (unsigned long long)__popcll(mystill),
+                                        0ull};
+#pragma unroll
+    for (uint32_t c = 0; c < kPer; ++c) {
+        if ((myfin >> c) & 1ull) {
+            sv[1] += cnt[c];
+            sv[2] += min(cnt[c], E.seg_cap);
+            sv[5] += cnt[c] > E.seg_cap ? 1u : 0u;
         }
     }
-    // exclusive prefix of the finished lanes' segment entry counts (sweep input)
+    unsigned long long tot[kScanVals];
+    block_scan_multi(sv, sm.mscan, tot);
+    const uint32_t F = (uint32_t)tot[0];
+    const unsigned long long R64 = tot[1], S64 = tot[2];
+    const uint32_t nstill = (uint32_t)tot[4];
+    const bool any_spill = tot[5] != 0;
+    // 3. each finished lane's row: staging range, sample index, entry of the fin
+    // list and its segment-entry prefix (the sweep's input)
     {
-        unsigned long long run = block_excl_scan(segsum, sm.bscan, S64);
-        for (uint32_t k = (uint32_t)k0; k < (uint32_t)k0 + (uint32_t)__popcll(myfin); ++k) {
-            ctl->fin_pre[k] = (uint32_t)run;
-            run += sm.lane[k];
+        unsigned long long rb = h.pair_cursor + sv[1], seg = sv[2];
+        uint32_t k = (uint32_t)sv[0];
+#pragma unroll
+        for (uint32_t c = 0; c < kPer; ++c) {
+            if ((myfin >> c) & 1ull) {
+                const uint32_t l = a0 + c, rc = cnt[c], j = jj[c];
+                ctl->retired_j[l] = j;
+                ctl->lane_base[l] = rb;
+                E.row_start[j] = rb;
+                E.row_len[j] = rc;
+                rb += rc;
+                ctl->lane_cnt[l] = 0;
+                ctl->fin_lane[k] = l;
+                ctl->fin_pre[k] = (uint32_t)seg;
+                seg += min(rc, E.seg_cap);
+                ++k;
+            }
         }
     }
-    const bool any_spill = __syncthreads_or(spilled);
     if (t < WB) ctl->fin_mask[t] = sm.sfin[t];
     // 4. refill: lanes without a sample take the next ids in lane order
-    const bool any_still = __syncthreads_or(mystill != 0);
-    const bool may_refill = h.err == 0 && (h.refill == kRefillLane || !any_still);
-    const unsigned long long need = may_refill ? (~mystill & (a0 < a1 ? runmask : 0ull)) : 0ull;
-    const unsigned long long r0 = block_excl_scan((unsigned long long)__popcll(need), sm.bscan, N64);
+    const bool may_refill = h.err == 0 && (h.refill == kRefillLane || nstill == 0);
     const unsigned long long avail = E.S > h.next_j ? E.S - h.next_j : 0ull;
-    {
-        unsigned long long r = r0, got = 0;
-        for (unsigned long long nd = need; nd && r < avail; nd &= nd - 1, ++r) {
-            const uint32_t c = __ffsll((long long)nd) - 1;
-            ctl->lane_j[a0 + c] = (uint32_t)(h.next_j + r);
-            got |= 1ull << c;
+    const unsigned long long N64 = may_refill ? tot[3] : 0ull;
+    const unsigned long long assigned = N64 < avail ? N64 : avail;
+    if (may_refill) {
+        unsigned long long r = sv[3], got = 0;
+#pragma unroll
+        for (uint32_t c = 0; c < kPer; ++c) {
+            if ((freem >> c) & 1ull) {
+                if (r < avail) {
+                    ctl->lane_j[a0 + c] = (uint32_t)(h.next_j + r);
+                    if (init) sm.lane[r] = a0 + c;  // r < L: the new lanes in lane order
+                    got |= 1ull << c;
+                }
+                ++r;
+            }
         }
         if (got) atomicOr(&sm.init[wi], got << (a0 & 63));
     }
-    block_excl_scan((unsigned long long)__popcll(mystill), sm.bscan, ST64);  // lanes still traversing
+    __syncthreads();
     if (t < WB) {
-        ctl->init_w[t] = sm.init[t];
+        ctl->init_w[t] = init ? 0ull : sm.init[t];
         ctl->run_w[t] = sm.still[t] | sm.init[t];
         ctl->still_w[t] = sm.still[t];
         ctl->act_w[t] = 0;
     }
-    const bool any_run = __syncthreads_or(t < WB && (sm.still[t] | sm.init[t]) != 0);
-    const uint32_t nstill = (uint32_t)ST64;
+    // the start vertices of the new lanes (Listing 1's frontier initialization)
+    if (init) {
+        for (uint32_t r = t; r < (uint32_t)assigned; r += blockDim.x) {
+            const uint32_t l = sm.lane[r];
+            const uint64_t j = h.next_j + r;
+            const uint32_t v = start_vertex(E.seed, E.first_id + j, E.n);
+            E.starts[j] = v;
+            or_next(E, v, l >> 6, 1ull << (l & 63));
+        }
+    }
+    const bool any_run = nstill != 0 || assigned != 0;
     // 5. direction of the coming level
     {
         const unsigned long long np = h.new_packed;
@@ -1023,7 +1074,6 @@ __device__ void dev_schedule(const Eng& E, Smem& sm) {
             ctl->spill_len[dst] = 0;
         }
         ctl->spill_sweep = any_spill ? 1u : 0u;
-        const unsigned long long assigned = N64 < avail ? N64 : avail;
         const unsigned long long tick = h.tick;
         if (E.trace && tick < E.trace_cap) {
             fbpt_trace_row& row = E.trace[tick];
@@ -1059,7 +1109,7 @@ __device__ void dev_schedule(const Eng& E, Smem& sm) {
         }
         ctl->new_packed = 0;
         ctl->chunk_next = 0;
-        ctl->pend_count = 0;
+        if (!init) ctl->pend_count = 0;
         ctl->tick = tick + 1;
         uint32_t run = any_run ? 1u : 0u;
         if (tick + 1 > h.tick_limit) {
@@ -1077,10 +1127,10 @@ __device__ void dev_schedule(const Eng& E, Smem& sm) {
 // ---- per-level kernels (host-driven or CUDA-graph loop) ------------------------------------
 
 __global__ void __launch_bounds__(kThreads) k_sweep(const Eng E) {
-    __shared__ Smem sm;
-    dev_sweep(E, sm);
+    __shared__ uint32_t pre[kMaxLanes + 1];
+    __shared__ uint64_t fin[kMaxWords];
+    dev_sweep(E, pre, fin);
 }
-__global__ void __launch_bounds__(kThreads) k_init(const Eng E) { dev_init(E); }
 __global__ void __launch_bounds__(kThreads, FBPT_EXPAND_MINB) k_expand(const Eng E) {
     __shared__ uint32_t lane_j[kMaxLanes];
     dev_expand<kPartPush>(E, lane_j);
@@ -1093,9 +1143,9 @@ __global__ void __launch_bounds__(kThreads) k_commit(const Eng E) {
     __shared__ Smem sm;
     dev_commit(E, sm);
 }
-__global__ void __launch_bounds__(kThreads) k_schedule(const Eng E) {
+__global__ void __launch_bounds__(kSchedThreads) k_schedule(const Eng E) {
     __shared__ Smem sm;
-    dev_schedule(E, sm);
+    dev_schedule<kMaxLanes / kSchedThreads, true>(E, sm);
 }
 
 // ---- persistent form: the whole run in one cooperative launch -------------------------------
@@ -1121,7 +1171,7 @@ __device__ bool grid_barrier(const Eng& E, Smem& sm, unsigned& gen, bool schedul
     __syncthreads();
     if (sm.last) {
         __threadfence();
-        if (schedule) dev_schedule(E, sm);
+        if (schedule) dev_schedule<kMaxLanes / kThreads, false>(E, sm);
         if (threadIdx.x == 0) {
             ctl->bar_count = 0;
             __threadfence();
@@ -1149,7 +1199,7 @@ __global__ void __launch_bounds__(kThreads) k_run(const Eng E) {
     Ctl* ctl = E.ctl;
     unsigned gen = 0;
     for (;;) {
-        dev_sweep(E, sm);  // lanes finished at the previous level
+        dev_sweep(E, sm.lane, sm.fin);  // lanes finished at the previous level
         dev_init(E);       // lanes given a sample at the previous level
         dev_expand<kPartAll>(E, sm.lane);
         if (!grid_barrier(E, sm, gen, false)) return;
@@ -1157,7 +1207,7 @@ __global__ void __launch_bounds__(kThreads) k_run(const Eng E) {
         if (!grid_barrier(E, sm, gen, true)) return;
         if (!L2(&ctl->running)) break;
     }
-    dev_sweep(E, sm);
+    dev_sweep(E, sm.lane, sm.fin);
 }
 
 // ---- final CSR: each staged row sorted into its place -----------------------------------
@@ -1325,13 +1375,26 @@ int order_rows(const uint32_t* rows_v, const uint64_t* row_start, const uint32_t
     return FBPT_OK;
 }
 
-int launch_level(const Eng& E, cudaStream_t st, int blocks) {
-    k_sweep<<<blocks, kThreads, 0, st>>>(E);
-    k_init<<<std::min(blocks, (int)(64 * E.WB + kThreads - 1) / kThreads), kThreads, 0, st>>>(E);
+// One level.  With a side stream (graph capture), the sweep runs on it beside
+// the expand: the sweep touches the finished lanes' segments, the spill log,
+// visited[], the RR staging rows and the counts; the expand reads the frontier
+// list, col/thr and the lanes' sample ids and writes next[], nocc[] and the
+// pending list, so the two may overlap; the commit waits for both.
+int launch_level(const Eng& E, cudaStream_t st, int blocks, cudaStream_t side = nullptr,
+                 cudaEvent_t fork = nullptr, cudaEvent_t join = nullptr) {
+    if (side) {
+        FBPT_CUDA_TRY(cudaEventRecord(fork, st));
+        FBPT_CUDA_TRY(cudaStreamWaitEvent(side, fork, 0));
+        k_sweep<<<blocks, kThreads, 0, side>>>(E);
+        FBPT_CUDA_TRY(cudaEventRecord(join, side));
+    } else {
+        k_sweep<<<blocks, kThreads, 0, st>>>(E);
+    }
     k_expand<<<blocks, kThreads, 0, st>>>(E);
     if (E.alt) k_expand_alt<<<blocks, kThreads, 0, st>>>(E);
+    if (side) FBPT_CUDA_TRY(cudaStreamWaitEvent(st, join, 0));
     k_commit<<<blocks, kThreads, 0, st>>>(E);
-    k_schedule<<<1, kThreads, 0, st>>>(E);
+    k_schedule<<<1, kSchedThreads, 0, st>>>(E);
     FBPT_CUDA_TRY(cudaGetLastError());
     return FBPT_OK;
 }
@@ -1369,18 +1432,31 @@ int add_level_loop(cudaGraph_t graph, const cudaGraphNode_t* deps, size_t ndeps,
     if (cudaGraphAddNode(node, graph, deps, nullptr, ndeps, &p) != cudaSuccess)
         return fail(FBPT_ECUDA, "cudaGraphAddNode(conditional) failed");
     cudaGraph_t body = p.conditional.phGraph_out[0];
-    cudaStream_t cs;
-    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess)
-        return fail(FBPT_ECUDA, "stream create failed");
+    cudaStream_t cs = nullptr, side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    auto release = [&]() {
+        if (fork) cudaEventDestroy(fork);
+        if (join) cudaEventDestroy(join);
+        if (side) cudaStreamDestroy(side);
+        if (cs) cudaStreamDestroy(cs);
+    };
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&join, cudaEventDisableTiming) != cudaSuccess) {
+        release();
+        cudaGetLastError();
+        return fail(FBPT_ECUDA, "stream or event create failed");
+    }
     E.cond = (unsigned long long)h;
     if (cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
-        cudaStreamDestroy(cs);
+        release();
         return fail(FBPT_ECUDA, "cudaStreamBeginCaptureToGraph failed");
     }
-    const int lrc = launch_level(E, cs, blocks);
+    const int lrc = launch_level(E, cs, blocks, side, fork, join);
     cudaGraph_t captured = nullptr;
     const cudaError_t ce = cudaStreamEndCapture(cs, &captured);
-    cudaStreamDestroy(cs);
+    release();
     if (lrc != FBPT_OK) return lrc;
     if (ce != cudaSuccess) return fail(FBPT_ECUDA, std::string("capture failed: ") + cudaGetErrorString(ce));
     return FBPT_OK;
