@@ -45,6 +45,9 @@ constexpr int kThreads = 256;
 #ifndef FBPT_EXPAND_ILP
 #define FBPT_EXPAND_ILP 1   // chunks a warp works on at once in the expand
 #endif
+#ifndef FBPT_COMMIT_VPW_MIN
+#define FBPT_COMMIT_VPW_MIN 8  // fewest pending vertices a commit warp takes
+#endif
 #ifndef FBPT_EXPAND_MINB
 #define FBPT_EXPAND_MINB 3  // resident CTAs per SM the expand kernel is compiled for
 #endif
@@ -609,10 +612,15 @@ __device__ void dev_commit(const Eng& E, Smem& sm) {
     Ctl* ctl = E.ctl;
     const uint32_t P = (uint32_t)min((uint64_t)L2(&ctl->pend_count), E.pend_cap);
     // vertices per warp: spread a small level over more warps of the grid (the
-    // work is a chain of dependent loads per vertex), but at least 8 per warp so
-    // that each warp's fixed bookkeeping stays amortised; up to one per lane
+    // work is a chain of dependent loads per vertex), but at least
+    // FBPT_COMMIT_VPW_MIN per warp so that each warp's fixed bookkeeping stays
+    // amortised; up to one per lane.  A warp takes every nused-th pending
+    // vertex (nused: the warps a round needs): the hubs, which many frontier
+    // units reach early in the expand and so head the pending list, are spread
+    // over the warps instead of lengthening the first warps' item loops.
     const uint64_t nwarp = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    const uint32_t vpw = (uint32_t)min((uint64_t)32, max((uint64_t)8, (P + nwarp - 1) / nwarp));
+    const uint32_t vpw =
+        (uint32_t)min((uint64_t)32, max((uint64_t)FBPT_COMMIT_VPW_MIN, (P + nwarp - 1) / nwarp));
     if ((uint64_t)blockIdx.x * (blockDim.x >> 5) * vpw >= P) return;  // no pending vertex for this CTA
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < 2 * E.WB; i += blockDim.x) sm.act[i] = 0;
@@ -623,9 +631,12 @@ __device__ void dev_commit(const Eng& E, Smem& sm) {
     const uint64_t wid = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     CommitWarp& cw = sm.cw[threadIdx.x >> 5];
     uint64_t mwords = 0, ncol = 0;
-    for (uint64_t base = wid * vpw; base < P; base += nwarp * vpw) {
-        const uint64_t idx = base + lane;
-        const bool ok = lane < vpw && idx < P;
+    for (uint64_t r0 = 0; r0 < P; r0 += nwarp * vpw) {
+        const uint64_t C = min((uint64_t)P - r0, nwarp * vpw);  // vertices of this round
+        const uint64_t nused = (C + vpw - 1) / vpw;
+        if (wid >= nused) break;  // only the last round leaves warps out
+        const uint64_t idx = r0 + wid + (uint64_t)lane * nused;
+        const bool ok = lane < vpw && idx < r0 + C;
         uint32_t w = 0;
         uint64_t m = 0, rs = 0, re = 0;
         if (ok) {
@@ -664,7 +675,7 @@ __device__ void dev_commit(const Eng& E, Smem& sm) {
                 nx &= ~vis;
                 if (nx) {
                     E.visited[rowi] = vis | nx;
-                    E.stage[(base + o) * E.WB + i] = nx;
+                    E.stage[(r0 + wid + (uint64_t)o * nused) * E.WB + i] = nx;
                     if (i < 32) atomicOr(&cw.occ_lo[o], 1u << i);
                     else atomicOr(&cw.occ_hi[o], 1u << (i - 32));
                     atomicAdd(&cw.bits[o], (uint32_t)__popcll(nx));
@@ -950,8 +961,6 @@ __device__ void dev_schedule(const Eng& E, Smem& sm) {
     const unsigned long long mystill = ((run & act) >> (a0 & 63)) & runmask;
     const unsigned long long freem = ~mystill & runmask;
     __syncthreads();
-    // the commit has consumed the pending list: the init below starts the next one
-    if (init && t == 0) ctl->pend_count = 0;
     // 2. per thread: finished lanes, their entries, segment entries, spilled
     // lanes; free and traversing lanes.  One scan gives every prefix.
     unsigned long long sv[kScanVals] = {(unsigned long long)__popcll(myfin), 0ull, 0ull,
@@ -1021,15 +1030,49 @@ __device__ void dev_schedule(const Eng& E, Smem& sm) {
         ctl->still_w[t] = sm.still[t];
         ctl->act_w[t] = 0;
     }
-    // the start vertices of the new lanes (Listing 1's frontier initialization)
+    // the start vertices of the new lanes (Listing 1's frontier initialization).
+    // The commit has cleared next[] and nocc[] of every row it took, so both are
+    // zero here: a lane sets its bits with two independent atomics, the lane
+    // that first marks nocc[v] lists v as pending, and the pending list (which
+    // the commit has consumed) restarts with these vertices at block-scan
+    // positions.
     if (init) {
-        for (uint32_t r = t; r < (uint32_t)assigned; r += blockDim.x) {
-            const uint32_t l = sm.lane[r];
-            const uint64_t j = h.next_j + r;
-            const uint32_t v = start_vertex(E.seed, E.first_id + j, E.n);
-            E.starts[j] = v;
-            or_next(E, v, l >> 6, 1ull << (l & 63));
+        const uint32_t lane = lane_id(), warp = t >> 5, nw = blockDim.x >> 5;
+        uint32_t listed = 0;
+        for (uint32_t base = 0; base < (uint32_t)assigned; base += blockDim.x) {
+            const uint32_t r = base + t;
+            uint32_t v = 0;
+            bool first = false;
+            if (r < (uint32_t)assigned) {
+                const uint32_t l = sm.lane[r];
+                const uint64_t j = h.next_j + r;
+                v = start_vertex(E.seed, E.first_id + j, E.n);
+                E.starts[j] = v;
+                const uint32_t i = l >> 6;
+                atomicOr((unsigned long long*)&E.next[(uint64_t)v * E.WB + i], 1ull << (l & 63));
+                first = atomicOr((unsigned long long*)&E.nocc[v], 1ull << i) == 0ull;
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, first);
+            if (lane == 0) sm.mscan[warp][0] = __popc(bal);
+            __syncthreads();
+            if (warp == 0) {
+                const unsigned long long x = lane < nw ? sm.mscan[lane][0] : 0ull;
+                const unsigned long long xi = warp_incl_scan(x);
+                if (lane < nw) sm.mscan[lane][0] = xi - x;
+                if (lane == 31) sm.mscan[32][0] = xi;
+            }
+            __syncthreads();
+            if (first) {
+                const uint64_t p = listed + sm.mscan[warp][0] + __popc(bal & lanemask_lt());
+                if (p < E.pend_cap)
+                    E.pend_v[p] = v;
+                else
+                    atomicOr(&ctl->error, (unsigned)kErrPendOverflow);
+            }
+            listed += (uint32_t)sm.mscan[32][0];
+            __syncthreads();
         }
+        if (t == 0) ctl->pend_count = listed;
     }
     const bool any_run = nstill != 0 || assigned != 0;
     // 5. direction of the coming level
@@ -1040,7 +1083,7 @@ __device__ void dev_schedule(const Eng& E, Smem& sm) {
         const uint32_t sched = h.sched;
         const bool pull_ok = E.frontd != nullptr;
         if (t == 0) {
-            level_features(sm.feat, U, G, C, (double)nstill, (double)E.m);
+            if (sched == FBPT_SCHED_LEARNED && E.policy) level_features(sm.feat, U, G, C, (double)nstill, (double)E.m);
             uint32_t d = kDirPush;
             if (sched == FBPT_SCHED_PULL && pull_ok) d = kDirPull;
             else if (sched == FBPT_SCHED_FILTERED) d = kDirFiltered;

@@ -18,7 +18,10 @@ constexpr uint64_t kSegBytesMax = 2ull << 30;  // largest segment array of a wor
 constexpr uint32_t kSpillPosBits = 26;
 constexpr uint64_t kSpillMask = (1ull << kSpillPosBits) - 1;
 constexpr uint32_t kChunk = 32;         // 4-edge groups per expand chunk (one per lane)
-constexpr uint32_t kChunksPerGrab = 2;  // chunks a warp takes per atomic
+#ifndef FBPT_CHUNKS_PER_GRAB
+#define FBPT_CHUNKS_PER_GRAB 2
+#endif
+constexpr uint32_t kChunksPerGrab = FBPT_CHUNKS_PER_GRAB;  // chunks a warp takes per atomic
 
 enum ErrorBits : uint32_t {
     kErrListOverflow = 1u,
