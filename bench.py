@@ -305,6 +305,44 @@ def main():
                "theta": ires["theta"], "rounds": ires["rounds"], "lower_bound": ires["lower_bound"],
                "coverage": ires["coverage"], "samples_per_s": ires["samples"] / dt}
 
+    # ---- the same step on a relabelled graph (Section 5: vertices by
+    # decreasing degree, samples taking lanes by start vertex); the order is
+    # host preprocessing like the graph upload, outside the timed steps, and
+    # the RR sets are the same bits ----
+    ordered = None
+    if rank == 0 and world == 1 and not args.no_plain:
+        try:
+            t0 = time.perf_counter()
+            perm = fbpt.order_compute(g.n, g.row_ptr, g.col, "degree")
+            host_s = time.perf_counter() - t0
+            dg.set_order(perm, True)
+            warm, _ = step()
+            ref_total = warm.total
+            del warm
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            osteps = max(1, min(args.steps, 3))
+            e0.record(stream)
+            for _ in range(osteps):
+                orr, _ = step()
+                ost = orr.stats
+                del orr
+            e1.record(stream)
+            torch.cuda.synchronize()
+            oms = e0.elapsed_time(e1) / osteps
+            ordered = {"order": "degree", "sorted_starts": True, "value": S / (oms / 1e3), "unit": "RR samples/s",
+                       "ms_per_step": oms, "steps": osteps, "host_order_s": host_s, "levels": int(ost.levels),
+                       "groups_expanded": int(ost.groups_expanded), "rr_total": int(ref_total),
+                       "same_rr_total": int(ref_total) == int(st.rr_total)}
+        except Exception as ex:  # reported, never fatal to the line
+            ordered = {"error": str(ex)[:200]}
+        finally:
+            try:
+                dg.set_order(None, False)
+            except Exception:
+                pass
+
     batched = None
     if rank == 0 and world == 1 and args.batched_steps > 0:
         batched = bench_batched(fbpt, torch, stream, args.batched_steps, args.schedule)
@@ -380,7 +418,7 @@ def main():
             "config": {"workload": args.workload, "graph": g.name, "n": g.n, "m": g.m, "samples_per_gpu": S, "k": k,
                        "shape": kw, "autotuned": tuned,
                        "l2": "inputs larger than L2 (in-CSR + thresholds %.0f MB)" % ((g.m * 8 + g.n * 8) / 1e6)},
-            "plain_fused": plain, "batched_32": batched, "imm": imm,
+            "plain_fused": plain, "ordered": ordered, "batched_32": batched, "imm": imm,
             "colour_edge_visits_per_s": st.colour_edge_visits * world / (ms_step / 1e3),
             "stats": st.as_dict(),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,

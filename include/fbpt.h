@@ -191,9 +191,48 @@ typedef struct fbpt_stats {
 int fbpt_graph_create(uint32_t n, uint64_t m, const uint64_t* row_ptr, const uint32_t* col,
                       const uint32_t* thr, int mem_kind, void* stream, fbpt_graph** out);
 int fbpt_graph_destroy(fbpt_graph* g);
-/* n, m and device addresses of the stored arrays (any pointer may be NULL). */
+/* n, m and device addresses of the stored arrays (any pointer may be NULL).
+ * While a vertex order is set (fbpt_graph_set_order), col holds relabelled
+ * sources (perm[u]); row_ptr and thr are never changed. */
 int fbpt_graph_info(const fbpt_graph* g, uint32_t* n, uint64_t* m, const uint64_t** row_ptr,
                     const uint32_t** col, const uint32_t** thr);
+
+/* ---- Vertex order (Section 5: reordering raises colour occupancy) ------------
+ * The paper relabels vertices (RCM, clustering) so that vertices reached
+ * together lie together, and lets the workers take start vertices from a
+ * sorted list.  Here a vertex order relabels only the device state that is
+ * indexed by vertex (the visited / next rows, the pending list, frontier
+ * units): the in-edges keep their in-CSR positions, so every liveness draw
+ * keeps its (sample id, edge index) counter and every result is unchanged.
+ * RR sets, starts and counts are returned in the caller's vertex ids. */
+enum fbpt_order_method {
+    FBPT_ORDER_IDENTITY = 0,  /* perm[v] = v */
+    FBPT_ORDER_RCM = 1,       /* reverse Cuthill-McKee over the undirected graph (u-v for every edge
+                                 u -> v, u != v): per component, a breadth-first search from an
+                                 unvisited vertex of least degree (ties: least id), neighbours taken
+                                 by increasing (degree, id); the order is then reversed */
+    FBPT_ORDER_DEGREE = 2,    /* by decreasing undirected degree, ties by id (hubs first) */
+    FBPT_ORDER_RANDOM = 3     /* a uniform permutation drawn from seed (the paper's baseline) */
+};
+/* Host only (needs no GPU): a vertex order of the graph given by its in-edge
+ * CSR (host arrays, the layout of fbpt_graph_create).  perm (n entries, caller
+ * owned) receives the new label of every vertex.  FBPT_EINVAL on a null
+ * array, an unknown method or a malformed CSR; FBPT_ENOMEM if the undirected
+ * adjacency (2m entries) cannot be allocated. */
+int fbpt_order_compute(uint32_t n, uint64_t m, const uint64_t* row_ptr, const uint32_t* col, uint32_t method,
+                       uint64_t seed, uint32_t* perm);
+/* Sets the vertex order of g: perm (host, n entries: perm[v] = new label of v)
+ * must be a permutation of 0 .. n-1 (FBPT_EINVAL otherwise); NULL restores the
+ * identity.  sorted_starts = 1 makes the samples of every later sampling call
+ * take lanes in increasing order of their (relabelled) start vertex, ties by
+ * sample id (Section 5's sorted start list), instead of in sample-id order.
+ * Pull levels are not available while a non-identity order is set: the pull
+ * schedule then fails with FBPT_EUNSUPPORTED and the heuristic and learned
+ * schedules choose between push and filtered push only.  Synchronous. */
+int fbpt_graph_set_order(fbpt_graph* g, const uint32_t* perm, uint32_t sorted_starts);
+/* The order set on g: perm (host, n entries, may be NULL) and sorted_starts
+ * (may be NULL). */
+int fbpt_graph_get_order(const fbpt_graph* g, uint32_t* perm, uint32_t* sorted_starts);
 
 /* ---- Sampling ----------------------------------------------------------------
  * RR sets of samples first_id .. first_id + S - 1 (Definition 2, computed by

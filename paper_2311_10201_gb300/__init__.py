@@ -129,6 +129,10 @@ _SIGS = {
     "fbpt_policy_loss_grad": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                              ctypes.c_uint64, ctypes.POINTER(ctypes.c_float), ctypes.c_void_p]),
     "fbpt_policy_get": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float), ctypes.c_uint64]),
+    "fbpt_order_compute": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_uint64, U64P, U32P, ctypes.c_uint32,
+                                          ctypes.c_uint64, U32P]),
+    "fbpt_graph_set_order": (ctypes.c_int, [ctypes.c_void_p, U32P, ctypes.c_uint32]),
+    "fbpt_graph_get_order": (ctypes.c_int, [ctypes.c_void_p, U32P, U32P]),
     "fbpt_last_error": (ctypes.c_char_p, []),
     "fbpt_version": (ctypes.c_int, []),
 }
@@ -209,6 +213,25 @@ class Graph:
     @classmethod
     def from_synth(cls, g, stream=None):
         return cls(g.n, g.row_ptr, g.col, g.thr, stream)
+
+    def set_order(self, perm=None, sorted_starts=False):
+        """Relabel the sampler's vertex state by perm (perm[v] = new label;
+        None = identity); sorted_starts: samples take lanes by start vertex.
+        Results are unchanged."""
+        p = None
+        if perm is not None:
+            p = np.ascontiguousarray(perm, np.uint32)
+            if p.size != self.n:
+                raise ValueError("perm must have n entries")
+            self._perm = p
+        _check(lib().fbpt_graph_set_order(self._h, _ptr_u32(p) if p is not None else None, int(bool(sorted_starts))))
+
+    def get_order(self):
+        """(perm, sorted_starts) currently set on the graph."""
+        p = np.zeros(self.n, np.uint32)
+        ss = ctypes.c_uint32()
+        _check(lib().fbpt_graph_get_order(self._h, _ptr_u32(p), ctypes.byref(ss)))
+        return p, bool(ss.value)
 
     def close(self):
         if self._h:
@@ -367,6 +390,21 @@ def imm(g: Graph, k: int, epsilon: float, ell: float, seed: int, max_samples: in
     _check(lib().fbpt_imm(g._h, k, float(epsilon), float(ell), seed, max_samples, ctypes.byref(o),
                           _ptr_u32(seeds), _ptr_u64(gains), ctypes.byref(res), ctypes.byref(st)))
     return seeds[:k], gains[:k], res.as_dict(), st
+
+
+ORDER = {"identity": 0, "rcm": 1, "degree": 2, "random": 3}
+
+
+def order_compute(n, row_ptr, col, method="rcm", seed=0):
+    """Host-side vertex order of an in-edge CSR (numpy arrays): perm[v] = new
+    label of v.  Needs no GPU."""
+    rp = np.ascontiguousarray(row_ptr, np.uint64)
+    c = np.ascontiguousarray(col, np.uint32)
+    perm = np.zeros(int(n), np.uint32)
+    meth = ORDER[method] if isinstance(method, str) else int(method)
+    _check(lib().fbpt_order_compute(int(n), int(c.size), _ptr_u64(rp), _ptr_u32(c) if c.size else None, meth,
+                                    int(seed), _ptr_u32(perm)))
+    return perm
 
 
 def select_seeds(rr: RRSets, k: int):

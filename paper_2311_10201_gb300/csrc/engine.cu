@@ -160,13 +160,15 @@ __device__ __forceinline__ void or_next(const Eng& E, uint32_t w, uint32_t i, ui
 // Only that entry writes the word during the sweep, so every other entry of
 // the word reads either all of the finished bits (and is not the lowest) or
 // none of them.
-__device__ __forceinline__ void sweep_entry(const Eng& E, const uint64_t* fin, uint32_t l, uint32_t v) {
+// v is the vertex's label in the sampler's order, vo its caller id (the same
+// without a vertex order).
+__device__ __forceinline__ void sweep_entry(const Eng& E, const uint64_t* fin, uint32_t l, uint32_t v, uint32_t vo) {
     const uint32_t w = l >> 6;
     unsigned long long* p = (unsigned long long*)&E.visited[(uint64_t)v * E.WB + w];
     const uint64_t m = L2(p) & fin[w];
     if (m == 0 || (uint32_t)(__ffsll((long long)m) - 1) != (l & 63u)) return;
     atomicAnd(p, ~(unsigned long long)m);
-    atomicAdd(&E.vcount[v], (uint32_t)__popcll(m));
+    atomicAdd(&E.vcount[vo], (uint32_t)__popcll(m));
 }
 
 // pre: shared memory for the finished lanes' entry prefixes (kMaxLanes + 1);
@@ -204,8 +206,9 @@ __device__ void dev_sweep(const Eng& E, uint32_t* pre, uint64_t* fin) {
             const uint32_t p = idx - pre[lo];
             const uint32_t v = L2(&E.seg[(uint64_t)l * E.seg_cap + p]);
             const uint64_t dst = L2(&ctl->lane_base[l]) + p;
-            if (dst < cap) E.rows_v[dst] = v;
-            sweep_entry(E, fin, l, v);
+            const uint32_t vo = E.inv ? __ldg(&E.inv[v]) : v;
+            if (dst < cap) E.rows_v[dst] = vo;
+            sweep_entry(E, fin, l, v, vo);
         }
     }
     if (spill) {
@@ -228,8 +231,9 @@ __device__ void dev_sweep(const Eng& E, uint32_t* pre, uint64_t* fin) {
             const uint64_t kp = warp_alloc<unsigned long long>(&ctl->spill_len[dst], (ok && !done) ? 1ull : 0ull);
             if (ok && done) {
                 const uint64_t d = L2(&ctl->lane_base[l]) + p;
-                if (d < cap) E.rows_v[d] = v;
-                sweep_entry(E, fin, l, v);
+                const uint32_t vo = E.inv ? __ldg(&E.inv[v]) : v;
+                if (d < cap) E.rows_v[d] = vo;
+                sweep_entry(E, fin, l, v, vo);
             } else if (ok) {
                 if (kp < E.spill_cap) E.spill[(uint64_t)dst * E.spill_cap + kp] = ent;
                 else atomicOr(&ctl->error, (unsigned)kErrSpillOverflow);
@@ -251,7 +255,7 @@ __device__ void dev_init(const Eng& E) {
         const uint32_t j = L2(&ctl->lane_j[l]);
         const uint32_t v = start_vertex(E.seed, E.first_id + j, E.n);
         E.starts[j] = v;
-        or_next(E, v, i, 1ull << c);
+        or_next(E, E.perm ? __ldg(&E.perm[v]) : v, i, 1ull << c);
     }
 }
 
@@ -504,6 +508,7 @@ __device__ __forceinline__ void expand_lt(const Eng& E, const uint32_t* lane_j, 
         const uint64_t occ = LD<ro>(&E.list_occ[u]);
         const uint32_t mrow = LD<ro>(&E.list_mrow[u]);
         const uint32_t v = LD<ro>(&E.list_v[u]);
+        const uint32_t vid = E.inv ? __ldg(&E.inv[v]) : v;  // the draw is keyed by the caller's vertex id
         const uint64_t rs = LD<ro>(&E.list_rs[u]), re = LD<ro>(&E.list_re[u]);
         const uint64_t base = __ldg(&E.wpre[rs]);
         const uint64_t total = __ldg(&E.wpre[re]) - base;
@@ -518,7 +523,7 @@ __device__ __forceinline__ void expand_lt(const Eng& E, const uint32_t* lane_j, 
                 const uint32_t j = lane_j[(i << 6) + c];
                 const uint32_t slo = f_lo + j;
                 const uint32_t shi = f_hi + (slo < j ? 1u : 0u);
-                const uint4 rnd = philox4x32_10(make_uint4(slo, shi, v, 0x40000000u), K);
+                const uint4 rnd = philox4x32_10(make_uint4(slo, shi, vid, 0x40000000u), K);
                 ++n_calls;
                 const uint64_t r = rnd.x;
                 if (r >= total) continue;  // v keeps no in-edge for this sample
@@ -643,8 +648,8 @@ __device__ void dev_commit(const Eng& E, Smem& sm) {
             w = L2(&E.pend_v[idx]);
             m = L2(&E.nocc[w]);
             E.nocc[w] = 0;
-            rs = __ldg(&E.row_ptr[w]);
-            re = __ldg(&E.row_ptr[w + 1]);
+            rs = __ldg(&E.rstart[w]);
+            re = __ldg(&E.rend[w]);
         }
         const uint32_t ni = __popcll(m);
         const uint32_t incl = warp_incl_scan(ni);
@@ -1014,7 +1019,7 @@ __device__ void dev_schedule(const Eng& E, Smem& sm) {
         for (uint32_t c = 0; c < kPer; ++c) {
             if ((freem >> c) & 1ull) {
                 if (r < avail) {
-                    ctl->lane_j[a0 + c] = (uint32_t)(h.next_j + r);
+                    ctl->lane_j[a0 + c] = E.order ? __ldg(&E.order[h.next_j + r]) : (uint32_t)(h.next_j + r);
                     if (init) sm.lane[r] = a0 + c;  // r < L: the new lanes in lane order
                     got |= 1ull << c;
                 }
@@ -1045,9 +1050,10 @@ __device__ void dev_schedule(const Eng& E, Smem& sm) {
             bool first = false;
             if (r < (uint32_t)assigned) {
                 const uint32_t l = sm.lane[r];
-                const uint64_t j = h.next_j + r;
-                v = start_vertex(E.seed, E.first_id + j, E.n);
-                E.starts[j] = v;
+                const uint64_t j = E.order ? (uint64_t)__ldg(&E.order[h.next_j + r]) : h.next_j + r;
+                const uint32_t v0 = start_vertex(E.seed, E.first_id + j, E.n);
+                E.starts[j] = v0;
+                v = E.perm ? __ldg(&E.perm[v0]) : v0;
                 const uint32_t i = l >> 6;
                 atomicOr((unsigned long long*)&E.next[(uint64_t)v * E.WB + i], 1ull << (l & 63));
                 first = atomicOr((unsigned long long*)&E.nocc[v], 1ull << i) == 0ull;
@@ -1638,6 +1644,7 @@ struct Run {
     uint64_t* row_start = nullptr;  // S
     uint32_t* row_len = nullptr;    // S
     fbpt_trace_row* dtrace = nullptr;
+    uint32_t* order = nullptr;      // S: sample index of each refill position (sorted starts), or NULL
     Ctl* H = nullptr;               // pinned: the initial control block in, the final one out
     Eng E = {};
 };
@@ -1657,10 +1664,12 @@ void run_release(Run& r, bool with_out) {
     if (r.row_start) cudaFreeAsync(r.row_start, r.st);
     if (r.row_len) cudaFreeAsync(r.row_len, r.st);
     if (r.dtrace) cudaFreeAsync(r.dtrace, r.st);
+    if (r.order) cudaFreeAsync(r.order, r.st);
     r.rows_v = nullptr;
     r.row_start = nullptr;
     r.row_len = nullptr;
     r.dtrace = nullptr;
+    r.order = nullptr;
     if (with_out) release_out(r.out);
 }
 
@@ -1704,10 +1713,12 @@ int run_setup(Run& r, fbpt_graph* g, uint64_t seed, uint64_t first_id, uint64_t 
             return fail(FBPT_EUNSUPPORTED, "fbpt_sample: the LT model runs fused push levels only");
         o.schedule = FBPT_SCHED_PUSH;
     }
-    // pull levels need dense frontier rows (WB <= 8 words), fused units and 32-bit edge ids
-    const bool pull_ok = WB <= kPullMaxWords && !o.unfused && g->m < (1ull << 32);
+    // pull levels need dense frontier rows (WB <= 8 words), fused units, 32-bit
+    // edge ids and the caller's vertex order
+    const bool pull_ok = WB <= kPullMaxWords && !o.unfused && g->m < (1ull << 32) && !g->perm;
     if (o.schedule == FBPT_SCHED_PULL && !pull_ok)
-        return fail(FBPT_EUNSUPPORTED, "fbpt_sample: pull needs words * slots <= 8, fused units and m < 2^32");
+        return fail(FBPT_EUNSUPPORTED,
+                    "fbpt_sample: pull needs words * slots <= 8, fused units, m < 2^32 and no vertex order");
     if (o.schedule == FBPT_SCHED_LEARNED && o.policy && !o.policy->d_params)
         return fail(FBPT_EINVAL, "fbpt_sample: policy has no parameters");
     if (o.launch != FBPT_LAUNCH_HOST && o.launch != FBPT_LAUNCH_GRAPH && o.launch != FBPT_LAUNCH_PERSISTENT)
@@ -1771,6 +1782,7 @@ int run_setup(Run& r, fbpt_graph* g, uint64_t seed, uint64_t first_id, uint64_t 
 int run_arm(Run& r) {
     fbpt_graph* g = r.g;
     Workspace* ws = r.ws;
+    if (g->sorted_starts && !r.order) FBPT_TRY(start_order(g, r.seed, r.first_id, r.S, r.st, &r.order));
     if (r.rows_v) cudaFreeAsync(r.rows_v, r.st);
     r.rows_v = nullptr;
     FBPT_CUDA_TRY(cudaMallocAsync(&r.rows_v, sizeof(uint32_t) * r.cap, r.st));
@@ -1789,6 +1801,11 @@ int run_arm(Run& r) {
     E = Eng{};
     E.n = g->n; E.WB = r.WB;
     E.row_ptr = g->row_ptr; E.col = g->col; E.thr = g->thr;
+    E.rstart = g->rstart ? g->rstart : g->row_ptr;
+    E.rend = g->rend ? g->rend : g->row_ptr + 1;
+    E.perm = g->perm;
+    E.inv = g->inv;
+    E.order = r.order;
     E.seed = r.seed; E.first_id = r.first_id; E.S = r.S;
     E.visited = ws->visited; E.next = ws->next; E.nocc = ws->nocc; E.stage = ws->stage;
     E.pend_v = ws->pend_v; E.seg = ws->seg; E.seg_cap = ws->seg_cap; E.spill = ws->spill;
@@ -1920,9 +1937,11 @@ int run_finish(Run& r, fbpt_stats* stats) {
     cudaFreeAsync(r.rows_v, st);
     cudaFreeAsync(r.row_start, st);
     cudaFreeAsync(r.row_len, st);
+    if (r.order) cudaFreeAsync(r.order, st);
     r.rows_v = nullptr;
     r.row_start = nullptr;
     r.row_len = nullptr;
+    r.order = nullptr;
     out->total = total;
     if (stats) {
         stats->levels += H->tick;

@@ -192,6 +192,11 @@ extern "C" int fbpt_graph_destroy(fbpt_graph* g) {
     cudaFree(g->row_ptr);
     cudaFree(g->col);
     cudaFree(g->thr);
+    cudaFree(g->perm);
+    cudaFree(g->inv);
+    cudaFree(g->col0);
+    cudaFree(g->rstart);
+    cudaFree(g->rend);
     delete g;
     return FBPT_OK;
 }

@@ -167,6 +167,15 @@ struct Eng {
     uint64_t trace_cap;
     unsigned long long cond;      // cudaGraphConditionalHandle (0 = host-driven loop)
     unsigned long long spin_limit;  // bounded waits of the persistent kernel's grid barrier
+    // vertex order: rows of vertex label w are [rstart[w], rend[w]) (row_ptr and
+    // row_ptr + 1 for the identity); perm maps a start vertex to its label and
+    // inv a label back (NULL for the identity); order[k] is the sample index
+    // the k-th refilled lane takes (NULL: k itself)
+    const uint64_t* rstart;
+    const uint64_t* rend;
+    const uint32_t* perm;
+    const uint32_t* inv;
+    const uint32_t* order;
 };
 
 }  // namespace fbpt
@@ -198,6 +207,13 @@ struct fbpt_graph {
     double rr_hint = 32.0;        // running estimate of RR entries per sample
     fbpt_tuning tuned = {};       // launch shape measured by fbpt_autotune
     bool tuned_valid = false;
+    // vertex order (fbpt_graph_set_order); all NULL for the identity
+    uint32_t* perm = nullptr;     // n: new label of each vertex
+    uint32_t* inv = nullptr;      // n: vertex of each new label
+    uint32_t* col0 = nullptr;     // m: the caller's sources (col then holds perm[col0])
+    uint64_t* rstart = nullptr;   // n: in-row start of each new label (row_ptr[inv[v']])
+    uint64_t* rend = nullptr;     // n: its end (row_ptr[inv[v'] + 1])
+    uint32_t sorted_starts = 0;   // samples take lanes by increasing (relabelled) start vertex
 };
 
 namespace fbpt {
@@ -217,4 +233,10 @@ int ensure_lt_weights(fbpt_graph* g, cudaStream_t st);
 // Device-wide exclusive scan of n counts into n+1 uint64 offsets (out[n] = total).
 int exclusive_scan_u32(const uint32_t* in, uint64_t* out, uint64_t n, cudaStream_t st);
 int exclusive_scan_u64(const uint64_t* in, uint64_t* out, uint64_t n, cudaStream_t st);
+// Stable LSD radix sort of n 64-bit keys on their low `bits` bits (tmp: n scratch keys).
+int radix_sort_u64(uint64_t* keys, uint64_t* tmp, uint64_t n, uint32_t bits, cudaStream_t st);
+// Device array order[S]: sample indices 0 .. S-1 by increasing (relabelled)
+// start vertex, ties by index (g->sorted_starts); caller frees with cudaFreeAsync.
+int start_order(const fbpt_graph* g, uint64_t seed, uint64_t first_id, uint64_t S, cudaStream_t st,
+                uint32_t** order);
 }  // namespace fbpt

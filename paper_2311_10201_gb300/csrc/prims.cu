@@ -1,5 +1,6 @@
-// Device-wide exclusive scans used by the sampler and the graph builder.
-// Three-phase (reduce, scan, apply): no kernel ever waits on another CTA.
+// Device-wide primitives used by the sampler and the graph builder: exclusive
+// scans and a stable LSD radix sort of 64-bit keys.  Three-phase designs
+// (reduce, scan, apply): no kernel ever waits on another CTA.
 #include "internal.cuh"
 
 namespace fbpt {
@@ -94,6 +95,79 @@ int scan_impl(const Tin* in, uint64_t* out, uint64_t n, cudaStream_t st) {
     return rc;
 }
 
+// ---- radix sort ---------------------------------------------------------------------
+
+constexpr int kRsWarps = 8;
+constexpr int kRsThreads = kRsWarps * 32;
+constexpr int kRsSteps = 16;                       // 32-key steps per warp
+constexpr uint64_t kRsTile = (uint64_t)kRsThreads * kRsSteps;
+
+__global__ void __launch_bounds__(kRsThreads) k_rs_hist(const uint64_t* keys, uint64_t n, uint32_t shift,
+                                                        uint32_t nblocks, uint32_t* hist) {
+    __shared__ uint32_t s_cnt[256];
+    s_cnt[threadIdx.x] = 0;
+    __syncthreads();
+    const uint64_t base = (uint64_t)blockIdx.x * kRsTile;
+    for (uint32_t i = threadIdx.x; i < kRsTile; i += kRsThreads) {
+        const uint64_t k = base + i;
+        if (k < n) atomicAdd(&s_cnt[(keys[k] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    hist[(uint64_t)threadIdx.x * nblocks + blockIdx.x] = s_cnt[threadIdx.x];
+}
+
+// Stable scatter: warp w of block b owns keys [b*tile + w*512, +512) and walks
+// them in order; equal digits are ranked with match_any within each 32-key step.
+__global__ void __launch_bounds__(kRsThreads) k_rs_scatter(const uint64_t* in, uint64_t* out, uint64_t n,
+                                                           uint32_t shift, uint32_t nblocks, const uint64_t* off) {
+    __shared__ uint32_t s_w[kRsWarps][256];
+    __shared__ uint64_t s_off[256];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < kRsWarps * 256; i += kRsThreads) (&s_w[0][0])[i] = 0;
+    __syncthreads();
+    const uint64_t wbase = (uint64_t)blockIdx.x * kRsTile + (uint64_t)warp * (32 * kRsSteps);
+    const uint32_t lt = lanemask_lt();
+    // A: per-warp digit counts
+    for (int step = 0; step < kRsSteps; ++step) {
+        const uint64_t k = wbase + (uint64_t)step * 32 + lane;
+        const bool ok = k < n;
+        const uint32_t d = ok ? (uint32_t)((in[k] >> shift) & 255u) : 256u + lane;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        if (ok && (peers & lt) == 0) s_w[warp][d] += __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    // B: per-warp bases relative to the block's digit offsets
+    {
+        const uint32_t d = threadIdx.x;  // 256 threads = 256 digits
+        s_off[d] = off[(uint64_t)d * nblocks + blockIdx.x];
+        uint32_t run = 0;
+        for (int w = 0; w < kRsWarps; ++w) {
+            const uint32_t c = s_w[w][d];
+            s_w[w][d] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    // C: scatter in order
+    for (int step = 0; step < kRsSteps; ++step) {
+        const uint64_t k = wbase + (uint64_t)step * 32 + lane;
+        const bool ok = k < n;
+        const uint64_t key = ok ? in[k] : 0;
+        const uint32_t d = ok ? (uint32_t)((key >> shift) & 255u) : 256u + lane;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        uint32_t rel = 0;
+        if (ok) rel = s_w[warp][d];
+        __syncwarp();
+        if (ok) {
+            const uint64_t pos = s_off[d] + rel + __popc(peers & lt);
+            out[pos] = key;
+            if ((peers & lt) == 0) s_w[warp][d] = rel + __popc(peers);
+        }
+        __syncwarp();
+    }
+}
+
 }  // namespace
 
 int exclusive_scan_u32(const uint32_t* in, uint64_t* out, uint64_t n, cudaStream_t st) {
@@ -102,6 +176,40 @@ int exclusive_scan_u32(const uint32_t* in, uint64_t* out, uint64_t n, cudaStream
 
 int exclusive_scan_u64(const uint64_t* in, uint64_t* out, uint64_t n, cudaStream_t st) {
     return scan_impl<uint64_t>(in, out, n, st);
+}
+
+int radix_sort_u64(uint64_t* keys, uint64_t* tmp, uint64_t n, uint32_t bits, cudaStream_t st) {
+    if (n <= 1 || bits == 0) return FBPT_OK;
+    const uint64_t nb64 = (n + kRsTile - 1) / kRsTile;
+    if (nb64 > 0xFFFFFFFFull / 256) return fail(FBPT_EUNSUPPORTED, "radix sort: too many keys");
+    const uint32_t nb = (uint32_t)nb64;
+    uint32_t* hist = nullptr;
+    uint64_t* off = nullptr;
+    if (cudaMallocAsync(&hist, sizeof(uint32_t) * 256ull * nb, st) != cudaSuccess ||
+        cudaMallocAsync(&off, sizeof(uint64_t) * (256ull * nb + 1), st) != cudaSuccess) {
+        if (hist) cudaFreeAsync(hist, st);
+        cudaGetLastError();
+        return fail(FBPT_ENOMEM, "radix sort: scratch allocation failed");
+    }
+    uint64_t* a = keys;
+    uint64_t* b = tmp;
+    int rc = FBPT_OK;
+    for (uint32_t shift = 0; shift < bits && rc == FBPT_OK; shift += 8) {
+        k_rs_hist<<<nb, kRsThreads, 0, st>>>(a, n, shift, nb, hist);
+        rc = exclusive_scan_u32(hist, off, 256ull * nb, st);
+        if (rc != FBPT_OK) break;
+        k_rs_scatter<<<nb, kRsThreads, 0, st>>>(a, b, n, shift, nb, off);
+        if (cudaGetLastError() != cudaSuccess) rc = fail(FBPT_ECUDA, "radix sort launch failed");
+        uint64_t* t = a;
+        a = b;
+        b = t;
+    }
+    if (rc == FBPT_OK && a != keys)
+        if (cudaMemcpyAsync(keys, a, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+            rc = fail(FBPT_ECUDA, "radix sort copy failed");
+    cudaFreeAsync(hist, st);
+    cudaFreeAsync(off, st);
+    return rc;
 }
 
 }  // namespace fbpt
