@@ -212,7 +212,17 @@ enum fbpt_order_method {
                                  unvisited vertex of least degree (ties: least id), neighbours taken
                                  by increasing (degree, id); the order is then reversed */
     FBPT_ORDER_DEGREE = 2,    /* by decreasing undirected degree, ties by id (hubs first) */
-    FBPT_ORDER_RANDOM = 3     /* a uniform permutation drawn from seed (the paper's baseline) */
+    FBPT_ORDER_RANDOM = 3,    /* a uniform permutation drawn from seed (the paper's baseline) */
+    FBPT_ORDER_CLUSTER = 4    /* communities of the undirected graph contiguous (the paper's
+                                 clustering order, Grappolo, is parallel Louvain): Louvain modularity
+                                 optimisation (Blondel et al. 2008), vertices moved in id order to the
+                                 neighbouring community of largest gain (ties: the lower community id;
+                                 a vertex stays unless the gain is positive), levels aggregated until
+                                 a level moves nothing (at most 8 levels; passes repeat until at
+                                 most 0.1 % of the nodes move, at most 16 per level).
+                                 Communities are laid out by decreasing total degree (ties: least
+                                 member id), recursively by level; vertices within the finest
+                                 community by decreasing degree, then id */
 };
 /* Host only (needs no GPU): a vertex order of the graph given by its in-edge
  * CSR (host arrays, the layout of fbpt_graph_create).  perm (n entries, caller

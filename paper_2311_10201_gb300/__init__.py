@@ -392,7 +392,7 @@ def imm(g: Graph, k: int, epsilon: float, ell: float, seed: int, max_samples: in
     return seeds[:k], gains[:k], res.as_dict(), st
 
 
-ORDER = {"identity": 0, "rcm": 1, "degree": 2, "random": 3}
+ORDER = {"identity": 0, "rcm": 1, "degree": 2, "random": 3, "cluster": 4}
 
 
 def order_compute(n, row_ptr, col, method="rcm", seed=0):

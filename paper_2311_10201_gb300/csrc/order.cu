@@ -1,6 +1,6 @@
 // Vertex orders (Section 5: relabelling the vertices so that vertices reached
 // together lie together, and a sorted list of start vertices): reverse
-// Cuthill-McKee, degree and random orders computed on the host, their
+// Cuthill-McKee, degree, random and Louvain clustering orders computed on the host, their
 // application to a graph's device state, and the sorted start list of a
 // sampling call.
 //
@@ -144,6 +144,179 @@ void random_order(uint32_t n, uint64_t seed, uint32_t* perm) {
     }
 }
 
+// ---- clustering order: Louvain (Blondel, Guillaume, Lambiotte and Lefebvre,
+// J. Stat. Mech. 2008), the sequential form of Section 5's Grappolo ----
+
+// One level's graph: symmetric weighted adjacency (integer weights), each
+// node's self-loop weight (internal edges of its community, counted from both
+// ends) and its degree k = incident weights + self-loop weight.
+struct LevelGraph {
+    uint32_t n = 0;
+    std::vector<uint64_t> off;
+    std::vector<uint32_t> adj;
+    std::vector<uint64_t> wt;
+    std::vector<uint64_t> self_w;
+    std::vector<uint64_t> k;
+};
+
+// Local moving: nodes in id order, each to the neighbouring community of the
+// largest modularity gain k_i,c - tot_c * k_i / 2m (compared exactly, scaled by
+// 2m); a node stays unless another community's gain is larger, ties between
+// other communities go to the lower id.  Passes repeat until at most 0.1 % of
+// the nodes move (at most 16).  Returns whether any node moved.
+bool local_moving(const LevelGraph& G, uint64_t two_m, std::vector<uint32_t>& comm) {
+    const uint32_t n = G.n;
+    comm.resize(n);
+    std::vector<uint64_t> tot(n);
+    for (uint32_t i = 0; i < n; ++i) {
+        comm[i] = i;
+        tot[i] = G.k[i];
+    }
+    std::vector<uint64_t> nw(n, 0);
+    std::vector<uint32_t> touched;
+    bool moved_any = false;
+    for (int pass = 0; pass < 16; ++pass) {
+        uint64_t moves = 0;
+        for (uint32_t i = 0; i < n; ++i) {
+            const uint32_t ci = comm[i];
+            touched.clear();
+            for (uint64_t a = G.off[i]; a < G.off[i + 1]; ++a) {
+                const uint32_t j = G.adj[a];
+                if (j == i) continue;
+                const uint32_t c = comm[j];
+                if (nw[c] == 0) touched.push_back(c);
+                nw[c] += G.wt[a];
+            }
+            tot[ci] -= G.k[i];
+            auto gain = [&](uint32_t c) {
+                return (__int128)nw[c] * (__int128)two_m - (__int128)tot[c] * (__int128)G.k[i];
+            };
+            uint32_t best = ci;
+            __int128 best_gain = gain(ci);
+            for (uint32_t c : touched) {
+                if (c == ci) continue;
+                const __int128 g = gain(c);
+                if (g > best_gain || (g == best_gain && best != ci && c < best)) {
+                    best = c;
+                    best_gain = g;
+                }
+            }
+            tot[best] += G.k[i];
+            if (best != ci) {
+                comm[i] = best;
+                ++moves;
+            }
+            for (uint32_t c : touched) nw[c] = 0;
+        }
+        if (moves) moved_any = true;
+        if (moves * 1000 <= n) break;  // fewer than 0.1 % of the nodes moved: the level has settled
+    }
+    return moved_any;
+}
+
+// Renumbers the communities 0 .. C-1 by first appearance in node order (ids
+// written back into comm) and builds the community graph.
+LevelGraph aggregate(const LevelGraph& G, std::vector<uint32_t>& comm) {
+    const uint32_t n = G.n;
+    std::vector<uint32_t> id(n, 0xFFFFFFFFu);
+    uint32_t C = 0;
+    for (uint32_t i = 0; i < n; ++i) {
+        if (id[comm[i]] == 0xFFFFFFFFu) id[comm[i]] = C++;
+        comm[i] = id[comm[i]];
+    }
+    // members of each community, in node order
+    std::vector<uint64_t> moff((size_t)C + 1, 0);
+    for (uint32_t i = 0; i < n; ++i) ++moff[comm[i] + 1];
+    for (uint32_t c = 0; c < C; ++c) moff[c + 1] += moff[c];
+    std::vector<uint32_t> mem(n);
+    {
+        std::vector<uint64_t> cur(moff.begin(), moff.end() - 1);
+        for (uint32_t i = 0; i < n; ++i) mem[cur[comm[i]]++] = i;
+    }
+    LevelGraph H;
+    H.n = C;
+    H.off.assign((size_t)C + 1, 0);
+    H.self_w.assign(C, 0);
+    H.k.assign(C, 0);
+    std::vector<uint64_t> nw(C, 0);
+    std::vector<uint32_t> touched;
+    for (uint32_t c = 0; c < C; ++c) {
+        touched.clear();
+        for (uint64_t a = moff[c]; a < moff[c + 1]; ++a) {
+            const uint32_t i = mem[a];
+            H.self_w[c] += G.self_w[i];
+            H.k[c] += G.k[i];
+            for (uint64_t e = G.off[i]; e < G.off[i + 1]; ++e) {
+                const uint32_t d = comm[G.adj[e]];
+                if (d == c) {
+                    H.self_w[c] += G.wt[e];
+                    continue;
+                }
+                if (nw[d] == 0) touched.push_back(d);
+                nw[d] += G.wt[e];
+            }
+        }
+        std::sort(touched.begin(), touched.end());
+        for (uint32_t d : touched) {
+            H.adj.push_back(d);
+            H.wt.push_back(nw[d]);
+            nw[d] = 0;
+        }
+        H.off[c + 1] = H.adj.size();
+    }
+    return H;
+}
+
+void cluster_order(uint32_t n, const std::vector<uint64_t>& off, const std::vector<uint32_t>& adj, uint32_t* perm) {
+    LevelGraph G;
+    G.n = n;
+    G.off = off;
+    G.adj = adj;
+    G.wt.assign(adj.size(), 1);
+    G.self_w.assign(n, 0);
+    G.k.resize(n);
+    for (uint32_t v = 0; v < n; ++v) G.k[v] = off[v + 1] - off[v];
+    const uint64_t two_m = adj.size();
+    // node of each vertex at every level; total degree and least member id of each node
+    std::vector<std::vector<uint32_t>> node_of;   // [level][vertex]
+    std::vector<std::vector<uint64_t>> tot_of;    // [level][node]
+    std::vector<std::vector<uint32_t>> minid_of;  // [level][node]
+    std::vector<uint32_t> cur(n);
+    for (uint32_t v = 0; v < n; ++v) cur[v] = v;
+    node_of.push_back(cur);
+    tot_of.push_back(G.k);
+    {
+        std::vector<uint32_t> ids(n);
+        for (uint32_t v = 0; v < n; ++v) ids[v] = v;
+        minid_of.push_back(ids);
+    }
+    std::vector<uint32_t> comm;
+    for (int level = 0; level < 8 && two_m > 0; ++level) {
+        if (!local_moving(G, two_m, comm)) break;
+        LevelGraph H = aggregate(G, comm);
+        for (uint32_t v = 0; v < n; ++v) cur[v] = comm[cur[v]];
+        std::vector<uint32_t> minid(H.n, 0xFFFFFFFFu);
+        for (uint32_t v = 0; v < n; ++v) minid[cur[v]] = std::min(minid[cur[v]], v);
+        node_of.push_back(cur);
+        tot_of.push_back(H.k);
+        minid_of.push_back(minid);
+        G = std::move(H);
+    }
+    const int L = (int)node_of.size();
+    std::vector<uint32_t> ids(n);
+    for (uint32_t v = 0; v < n; ++v) ids[v] = v;
+    std::sort(ids.begin(), ids.end(), [&](uint32_t a, uint32_t b) {
+        for (int l = L - 1; l >= 0; --l) {
+            const uint32_t x = node_of[l][a], y = node_of[l][b];
+            if (x == y) continue;
+            if (tot_of[l][x] != tot_of[l][y]) return tot_of[l][x] > tot_of[l][y];
+            return minid_of[l][x] < minid_of[l][y];
+        }
+        return false;
+    });
+    for (uint32_t i = 0; i < n; ++i) perm[ids[i]] = i;
+}
+
 __global__ void k_relabel(const uint32_t* perm, const uint64_t* row_ptr, const uint32_t* col0, uint32_t n,
                           uint64_t m, uint32_t* col, uint32_t* inv, uint64_t* rstart, uint64_t* rend) {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -226,7 +399,7 @@ using namespace fbpt;
 extern "C" int fbpt_order_compute(uint32_t n, uint64_t m, const uint64_t* row_ptr, const uint32_t* col,
                                   uint32_t method, uint64_t seed, uint32_t* perm) {
     if (n == 0 || !row_ptr || !perm || (m && !col)) return fail(FBPT_EINVAL, "fbpt_order_compute: null array or n = 0");
-    if (method > FBPT_ORDER_RANDOM) return fail(FBPT_EINVAL, "fbpt_order_compute: unknown method");
+    if (method > FBPT_ORDER_CLUSTER) return fail(FBPT_EINVAL, "fbpt_order_compute: unknown method");
     if (!csr_ok(n, m, row_ptr, col)) return fail(FBPT_EINVAL, "fbpt_order_compute: malformed CSR");
     try {
         switch (method) {
@@ -243,6 +416,13 @@ extern "C" int fbpt_order_compute(uint32_t n, uint64_t m, const uint64_t* row_pt
             case FBPT_ORDER_DEGREE:
                 degree_order(n, row_ptr, col, perm);
                 break;
+            case FBPT_ORDER_CLUSTER: {
+                std::vector<uint64_t> off;
+                std::vector<uint32_t> adj;
+                undirected(n, row_ptr, col, off, adj);
+                cluster_order(n, off, adj, perm);
+                break;
+            }
             default:
                 random_order(n, seed, perm);
                 break;

@@ -4,7 +4,8 @@ recovers a banded labelling of a shuffled path (bandwidth 1) and of a shuffled
 grid (no wider than the grid's side), keeps each connected component
 contiguous, and is no wider than scipy's RCM on random graphs; the degree order
 is non-increasing in degree with ties by id; the random order is a seeded,
-uniform-looking shuffle.  No GPU."""
+uniform-looking shuffle; the clustering (Louvain) order lays planted
+communities out contiguously, larger ones first.  No GPU."""
 import numpy as np
 import pytest
 
@@ -35,7 +36,7 @@ def shuffled(n, edges, seed):
     return [(int(lab[u]), int(lab[v])) for u, v in edges]
 
 
-@pytest.mark.parametrize("method", ["identity", "rcm", "degree", "random"])
+@pytest.mark.parametrize("method", ["identity", "rcm", "degree", "random", "cluster"])
 def test_every_method_gives_a_permutation(method):
     g = synth.rmat_wc(10)
     p = fbpt.order_compute(g.n, g.row_ptr, g.col, method, 3)
@@ -130,3 +131,35 @@ def test_bad_arguments_rejected():
     with pytest.raises(fbpt.FbptError) as ei:
         fbpt.order_compute(g.n, g.row_ptr, bad, "rcm")
     assert ei.value.code == fbpt.EINVAL
+
+
+def test_cluster_order_lays_out_planted_communities():
+    # cliques of different sizes joined in a ring by single edges, labels shuffled:
+    # Louvain keeps each clique a community, laid out contiguously, bigger first
+    sizes = [14, 9, 12, 7, 11, 8, 10, 13]
+    edges, start = [], 0
+    starts = []
+    for sz in sizes:
+        starts.append(start)
+        edges += [(start + a, start + b) for a in range(sz) for b in range(a + 1, sz)]
+        start += sz
+    n = start
+    for i in range(len(sizes)):
+        edges.append((starts[i], starts[(i + 1) % len(sizes)]))
+    edges = shuffled(n, edges, 4)
+    rp, col = in_csr(n, edges)
+    p = fbpt.order_compute(n, rp, col, "cluster")
+    lab = np.random.default_rng(4).permutation(n)
+    first = []
+    for st, sz in zip(starts, sizes):
+        labels = sorted(int(p[lab[st + x]]) for x in range(sz))
+        assert labels == list(range(labels[0], labels[0] + sz))
+        first.append(labels[0])
+    by_pos = [sz for _, sz in sorted(zip(first, sizes))]
+    assert by_pos == sorted(sizes, reverse=True)
+
+
+def test_cluster_order_without_edges_is_the_identity():
+    n = 50
+    p = fbpt.order_compute(n, np.zeros(n + 1, np.uint64), np.zeros(0, np.uint32), "cluster")
+    assert np.array_equal(p, np.arange(n))

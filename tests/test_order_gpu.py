@@ -45,7 +45,7 @@ def ordered(fbpt, g, method, sorted_starts, seed=9):
     return dg
 
 
-@pytest.mark.parametrize("method", ["rcm", "degree", "random"])
+@pytest.mark.parametrize("method", ["rcm", "degree", "random", "cluster"])
 @pytest.mark.parametrize("sorted_starts", [False, True])
 @pytest.mark.parametrize("launch", ["graph", "host", "persistent"])
 def test_ordered_graph_bit_exact(fbpt, wc13, method, sorted_starts, launch):
