@@ -362,34 +362,32 @@ int start_order(const fbpt_graph* g, uint64_t seed, uint64_t first_id, uint64_t 
     uint64_t* keys = nullptr;
     uint64_t* tmp = nullptr;
     uint32_t* out = nullptr;
-    auto undo = [&](int code, const char* what) {
+    auto release = [&](bool with_out) {
         if (keys) cudaFreeAsync(keys, st);
         if (tmp) cudaFreeAsync(tmp, st);
-        if (out) cudaFreeAsync(out, st);
-        cudaGetLastError();
-        return fail(code, std::string("sorted starts: ") + what);
+        if (with_out && out) cudaFreeAsync(out, st);
     };
     if (cudaMallocAsync(&keys, sizeof(uint64_t) * S, st) != cudaSuccess ||
         cudaMallocAsync(&tmp, sizeof(uint64_t) * S, st) != cudaSuccess ||
-        cudaMallocAsync(&out, sizeof(uint32_t) * S, st) != cudaSuccess)
-        return undo(FBPT_ENOMEM, "allocation failed");
+        cudaMallocAsync(&out, sizeof(uint32_t) * S, st) != cudaSuccess) {
+        release(true);
+        cudaGetLastError();
+        return fail(FBPT_ENOMEM, "sorted starts: allocation failed");
+    }
     const unsigned blocks = (unsigned)std::min<uint64_t>((S + 255) / 256, (uint64_t)device_sm_count() * 8);
     k_start_keys<<<blocks, 256, 0, st>>>(seed, first_id, S, g->n, g->perm, keys);
+    // the label occupies the low bits (whole bytes), the sample index the high
+    // 32: a stable sort on the label keeps equal labels in index order
     uint32_t bits = 8;
     while (bits < 32 && (1ull << bits) < (uint64_t)g->n) bits += 8;
-    const int rc = radix_sort_u64(keys, tmp, S, bits, st);
-    if (rc != FBPT_OK) {
-        if (keys) cudaFreeAsync(keys, st);
-        if (tmp) cudaFreeAsync(tmp, st);
-        if (out) cudaFreeAsync(out, st);
-        return rc;
+    int rc = radix_sort_u64(keys, tmp, S, bits, st);
+    if (rc == FBPT_OK) {
+        k_key_index<<<blocks, 256, 0, st>>>(keys, S, out);
+        if (cudaGetLastError() != cudaSuccess) rc = fail(FBPT_ECUDA, "sorted starts: launch failed");
     }
-    k_key_index<<<blocks, 256, 0, st>>>(keys, S, out);
-    if (cudaGetLastError() != cudaSuccess) return undo(FBPT_ECUDA, "launch failed");
-    cudaFreeAsync(keys, st);
-    cudaFreeAsync(tmp, st);
-    *order = out;
-    return FBPT_OK;
+    release(rc != FBPT_OK);
+    if (rc == FBPT_OK) *order = out;
+    return rc;
 }
 
 }  // namespace fbpt
@@ -470,7 +468,13 @@ extern "C" int fbpt_graph_set_order(fbpt_graph* g, const uint32_t* perm, uint32_
             cudaGetLastError();
             return fail(FBPT_ENOMEM, "fbpt_graph_set_order: device allocation failed");
         }
-        if (g->m) FBPT_CUDA_TRY(cudaMemcpyAsync(g->col0, g->col, sizeof(uint32_t) * g->m, cudaMemcpyDeviceToDevice, st));
+        if (g->m && (cudaMemcpyAsync(g->col0, g->col, sizeof(uint32_t) * g->m, cudaMemcpyDeviceToDevice, st) !=
+                         cudaSuccess ||
+                     cudaStreamSynchronize(st) != cudaSuccess)) {
+            cudaFree(g->col0);
+            g->col0 = nullptr;
+            return fail(FBPT_ECUDA, std::string("fbpt_graph_set_order: ") + cudaGetErrorString(cudaGetLastError()));
+        }
     }
     if ((!g->perm && cudaMalloc(&g->perm, sizeof(uint32_t) * n) != cudaSuccess) ||
         (!g->inv && cudaMalloc(&g->inv, sizeof(uint32_t) * n) != cudaSuccess) ||
