@@ -383,6 +383,14 @@ int fbpt_policy_param_count(void);
 int fbpt_policy_create(const float* params, uint64_t count, fbpt_policy** out);
 int fbpt_policy_destroy(fbpt_policy* p);
 int fbpt_policy_get(const fbpt_policy* p, float* params, uint64_t count);
+/* Writes p's parameters to a text file, one number per line printed with
+ * "%.9g" (a float32 reads back exactly): the format of the package's shipped
+ * policy.  FBPT_EINVAL for a null argument or a file that cannot be written. */
+int fbpt_policy_save(const fbpt_policy* p, const char* path);
+/* Reads fbpt_policy_param_count() numbers separated by white space from a
+ * text file into a new policy (as fbpt_policy_create).  FBPT_EINVAL if the file
+ * cannot be read, holds a token that is not a number, or holds another count. */
+int fbpt_policy_load(const char* path, fbpt_policy** out);
 
 /* Training on trace rows (host arrays): features[rows][6] as above,
  * actions[rows] (the direction a level ran with), targets[rows] (its log2

@@ -129,6 +129,8 @@ _SIGS = {
     "fbpt_policy_loss_grad": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                              ctypes.c_uint64, ctypes.POINTER(ctypes.c_float), ctypes.c_void_p]),
     "fbpt_policy_get": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float), ctypes.c_uint64]),
+    "fbpt_policy_save": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p]),
+    "fbpt_policy_load": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(ctypes.c_void_p)]),
     "fbpt_order_compute": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_uint64, U64P, U32P, ctypes.c_uint32,
                                           ctypes.c_uint64, U32P]),
     "fbpt_graph_set_order": (ctypes.c_int, [ctypes.c_void_p, U32P, ctypes.c_uint32]),
@@ -438,6 +440,18 @@ class Policy:
         out = np.zeros(lib().fbpt_policy_param_count(), np.float32)
         _check(lib().fbpt_policy_get(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), out.size))
         return out
+
+    def save(self, path):
+        """Write the parameters as text (fbpt_policy_save)."""
+        _check(lib().fbpt_policy_save(self._h, os.fsencode(path)))
+
+    @classmethod
+    def load(cls, path):
+        """A policy read from a text file (fbpt_policy_load)."""
+        obj = cls.__new__(cls)
+        obj._h = ctypes.c_void_p()
+        _check(lib().fbpt_policy_load(os.fsencode(path), ctypes.byref(obj._h)))
+        return obj
 
     def close(self):
         if self._h:

@@ -4,8 +4,11 @@
 // of the output.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "internal.cuh"
 
@@ -46,6 +49,43 @@ extern "C" int fbpt_policy_get(const fbpt_policy* p, float* params, uint64_t cou
     if (!p || !params || count != want) return fail(FBPT_EINVAL, "fbpt_policy_get: bad arguments");
     std::memcpy(params, p->h_params, sizeof(float) * want);
     return FBPT_OK;
+}
+
+extern "C" int fbpt_policy_save(const fbpt_policy* p, const char* path) {
+    if (!p || !path) return fail(FBPT_EINVAL, "fbpt_policy_save: null argument");
+    FILE* f = std::fopen(path, "w");
+    if (!f) return fail(FBPT_EINVAL, std::string("fbpt_policy_save: cannot write ") + path);
+    const uint64_t want = 2 * kPolicyIn + kPolicyParams;
+    bool ok = true;
+    for (uint64_t i = 0; i < want && ok; ++i) ok = std::fprintf(f, "%.9g\n", (double)p->h_params[i]) > 0;
+    ok = (std::fclose(f) == 0) && ok;
+    return ok ? FBPT_OK : fail(FBPT_EINVAL, std::string("fbpt_policy_save: write failed on ") + path);
+}
+
+extern "C" int fbpt_policy_load(const char* path, fbpt_policy** out) {
+    if (!path || !out) return fail(FBPT_EINVAL, "fbpt_policy_load: null argument");
+    *out = nullptr;
+    FILE* f = std::fopen(path, "r");
+    if (!f) return fail(FBPT_EINVAL, std::string("fbpt_policy_load: cannot read ") + path);
+    const uint64_t want = 2 * kPolicyIn + kPolicyParams;
+    std::vector<float> v;
+    char tok[64];
+    bool bad = false;
+    while (std::fscanf(f, "%63s", tok) == 1) {
+        char* end = nullptr;
+        const float x = std::strtof(tok, &end);
+        if (end == tok || *end != '\0') {
+            bad = true;
+            break;
+        }
+        v.push_back(x);
+        if (v.size() > want) break;
+    }
+    std::fclose(f);
+    if (bad) return fail(FBPT_EINVAL, std::string("fbpt_policy_load: not a number in ") + path);
+    if (v.size() != want)
+        return fail(FBPT_EINVAL, "fbpt_policy_load: expected " + std::to_string(want) + " numbers in " + path);
+    return fbpt_policy_create(v.data(), want, out);
 }
 
 // ---- training ----------------------------------------------------------------------

@@ -129,3 +129,18 @@ def test_trained_network_gains_over_the_heuristic(fbpt):
                                                                tot["meas_h"] / tot["meas_l"]))
     assert tot["learned"] < 0.9 * tot["heuristic"]
     assert tot["meas_l"] < tot["meas_h"]
+
+
+def test_policy_file_round_trip(fbpt, tmp_path):
+    """The shipped policy loads through fbpt_policy_load, saves through
+    fbpt_policy_save and reads back to the same float32 parameters."""
+    ref = np.loadtxt(fbpt.DEFAULT_POLICY_FILE, dtype=np.float64).astype(np.float32)
+    p = fbpt.Policy.load(fbpt.DEFAULT_POLICY_FILE)
+    assert np.array_equal(p.params(), ref)
+    out = tmp_path / "policy.txt"
+    p.save(out)
+    assert np.array_equal(np.loadtxt(out, dtype=np.float64).astype(np.float32), ref)
+    q = fbpt.Policy.load(out)
+    assert np.array_equal(q.params(), ref)
+    p.close()
+    q.close()
