@@ -244,6 +244,8 @@ __device__ void dev_sweep(const Eng& E, uint32_t* pre, uint64_t* fin) {
 }
 
 // ---- init: start vertices of lanes given a new sample (Listing 1's frontier initialization) ------
+// The persistent kernel runs this over all its CTAs; in the per-level forms the
+// scheduler CTA places the start vertices itself (dev_schedule<.., true>).
 
 __device__ void dev_init(const Eng& E) {
     Ctl* ctl = E.ctl;
