@@ -343,6 +343,37 @@ def main():
             except Exception:
                 pass
 
+    # ---- the linear-threshold model on the same graph (WC weights sum to at
+    # most 1 per row): RR walks instead of cascades, same shape, seeds included ----
+    lt = None
+    if rank == 0 and world == 1 and not args.no_plain:
+        try:
+            lkw = dict(words=8, slots=8, refill="lane", schedule="push", launch=args.launch, model="lt")
+
+            def lt_step():
+                lrr = fbpt.sample(dg, seed, first, S, **lkw)
+                fbpt.select_seeds(lrr, k)
+                return lrr
+            warm = lt_step()
+            del warm
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            lsteps = max(1, min(args.steps, 2))
+            e0.record(stream)
+            for _ in range(lsteps):
+                lrr = lt_step()
+                lst = lrr.stats
+                ltotal = lrr.total
+                del lrr
+            e1.record(stream)
+            torch.cuda.synchronize()
+            lms = e0.elapsed_time(e1) / lsteps
+            lt = {"model": "lt", "value": S / (lms / 1e3), "unit": "RR samples/s", "ms_per_step": lms,
+                  "steps": lsteps, "levels": int(lst.levels), "rr_total": int(ltotal)}
+        except Exception as ex:  # reported, never fatal to the line
+            lt = {"error": str(ex)[:200]}
+
     batched = None
     if rank == 0 and world == 1 and args.batched_steps > 0:
         batched = bench_batched(fbpt, torch, stream, args.batched_steps, args.schedule)
@@ -418,7 +449,7 @@ def main():
             "config": {"workload": args.workload, "graph": g.name, "n": g.n, "m": g.m, "samples_per_gpu": S, "k": k,
                        "shape": kw, "autotuned": tuned,
                        "l2": "inputs larger than L2 (in-CSR + thresholds %.0f MB)" % ((g.m * 8 + g.n * 8) / 1e6)},
-            "plain_fused": plain, "ordered": ordered, "batched_32": batched, "imm": imm,
+            "plain_fused": plain, "ordered": ordered, "lt": lt, "batched_32": batched, "imm": imm,
             "colour_edge_visits_per_s": st.colour_edge_visits * world / (ms_step / 1e3),
             "stats": st.as_dict(),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
