@@ -29,13 +29,11 @@ sys.path.insert(0, ROOT)
 import synth  # noqa: E402
 
 WORKLOAD = "rmat_s22_wc"
-# DRAM bytes (read + write) per 4-edge group of a steady-state k_expand
-# launch, from the ncu capture summarised in
-# profiles/level_kernels_rmat_s20_wc.md (level 40 of the R-MAT s20 WC workload
-# at 64-word rows: 55,187,712 B read + 230,400 B written for 1,496,061 groups).
-# The bench scales it by its own groups per launch; None once the kernel has
-# changed since that capture.
-EXPAND_DRAM_BYTES_PER_GROUP = (55207680 + 223744) / 1496061
+# DRAM bytes (read + write) per 4-edge group of a k_expand launch, from an ncu
+# capture of the current kernel; the bench scales it by its own groups per
+# launch.  None when the kernel has changed since the last capture.
+EXPAND_DRAM_BYTES_PER_GROUP = None
+EXPAND_TRAFFIC_NOTE = "no capture of the current expand kernel yet"
 METRIC = "RR samples/s (bit-exact RR sets + greedy seeds, R-MAT s22 WC, 1,048,576 samples, k=100)"
 
 
@@ -181,6 +179,52 @@ def bench_batched(fbpt, torch, stream, steps, schedule):
             dg.close()
     return {"graphs": len(w.graphs), "samples": total, "steps": steps, **arms,
             "speedup": arms["learned_batched"]["value"] / arms["plain"]["value"]}
+
+
+def timed_calls(torch, stream, call, steps):
+    """call() once untimed, then `steps` calls between CUDA events on stream;
+    returns (ms per call, the last call's result)."""
+    res = call()
+    del res
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        res = call()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps, res
+
+
+def bench_fused_unfused(fbpt, torch, stream, steps):
+    """R-MAT s20 weighted cascade, 65,536 samples: the plain fused form of
+    Listing 1 in batches of W = 1, 2, 4, 8 words (64 W colours per batch, a new
+    batch when all have finished, push levels, one graph launch) against the
+    same samples unfused (one traversal unit per colour, every colour reading
+    every edge itself; the same kernels and bits).  RR samples/s and
+    colour-edge visits/s per arm; edge accesses are what Theorem 1 bounds."""
+    w = synth.rmat_s20_wc()
+    g, S, seed = w.graphs[0], w.S[0], w.seeds[0]
+    dg = fbpt.Graph.from_synth(g, stream)
+    out = {"workload": "rmat_s20_wc", "samples": S, "steps": steps}
+    for W in (1, 2, 4, 8):
+        row = {}
+        for arm, unf in (("fused", False), ("unfused", True)):
+            kw = dict(words=W, slots=1, refill="batch", schedule="push", launch="graph", unfused=unf)
+
+            def call():
+                rr = fbpt.sample(dg, seed, 0, S, **kw)
+                return rr.stats
+            ms, st = timed_calls(torch, stream, call, steps)
+            row[arm] = {"value": S / (ms / 1e3), "unit": "RR samples/s", "ms_per_step": ms,
+                        "colour_edge_visits_per_s": st.colour_edge_visits / (ms / 1e3),
+                        "edge_accesses": int(st.edge_accesses), "philox_calls": int(st.philox_calls),
+                        "levels": int(st.levels), "ms_expand": st.ms_expand}
+        row["fused_over_unfused"] = row["fused"]["value"] / row["unfused"]["value"]
+        out[f"W{W}"] = row
+    dg.close()
+    return out
 
 
 def main():
@@ -385,31 +429,43 @@ def main():
     if rank == 0 and world == 1 and args.batched_steps > 0:
         batched = bench_batched(fbpt, torch, stream, args.batched_steps, args.schedule)
 
-    # ---- roofline of the dominant kernel (expand), per launch ----
-    # The expand is bound by integer ALU (the Philox rounds).  Algorithmic work:
-    # 98 int32 ops per Philox4x32-10 call (10 rounds x (2 mul-hi + 2 mul-lo +
-    # 4 xor) + 9 x 2 key adds).  Peak: 152 SMs x 128 int32 lanes x 2.07 GHz.
+    # ---- roofline of the dominant kernel (the push expand), per launch ----
+    # HBM is the roofline: nothing on the path is a dense contraction.
+    # Algorithmic bytes of one launch: 8 B of col + thr per in-edge read (edge
+    # accesses), 40 B per frontier unit (its record and chunk-map entry), 8 B per
+    # colour word of a unit (stage word).  The launch duration is measured with
+    # CUDA events around every expand launch of one host-launched call of the
+    # same shape right after the timed steps (inside the timed graph launch all
+    # levels run within one launch); the device %globaltimer brackets of the
+    # expand in the timed steps are reported beside it.  Secondary view: the
+    # liveness draws against the measured rate of a Philox-only kernel.
     launches = max(int(st.push_levels), 1)
-    exp_s = st.ms_expand * 1e-3
-    ops_per_launch = 98.0 * st.philox_calls / launches
-    achieved = 98.0 * st.philox_calls / exp_s / 1e12 if exp_s > 0 else 0.0
-    alu_peak = 152 * 128 * 2.07e9 / 1e12
     alg_bytes = (8 * st.edge_accesses + 40 * st.units_expanded + 8 * st.mask_words) / launches
-    hbm_gbs = alg_bytes * launches / exp_s / 1e9 if exp_s > 0 else 0.0
     pk, pk_kind = peaks()
-    roof = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s (int32)",
-            "frac": achieved / alu_peak,
+    ev_rr = fbpt.sample(dg, seed, first, S, **dict(kw, launch="host"))
+    ev = ev_rr.stats
+    del ev_rr
+    ev_launches = max(int(ev.push_levels), 1)
+    launch_s = ev.ms_expand_events * 1e-3 / ev_launches
+    achieved = alg_bytes / launch_s / 1e9 if launch_s > 0 else 0.0
+    exp_s = st.ms_expand * 1e-3
+    philox_peak = fbpt.philox_rate(seed, 16384)
+    calls_s = st.philox_calls / exp_s if exp_s else 0.0
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": achieved / pk["hbm_gbs"],
             "traffic": (EXPAND_DRAM_BYTES_PER_GROUP * st.groups_expanded / launches
                         if EXPAND_DRAM_BYTES_PER_GROUP else None),
-            "traffic_note": "ncu DRAM bytes per group on the s20 capture x this run's groups per launch",
-            "kernel": "k_expand",
-            "peak_kind": "derived: 152 SMs x 128 int32 lanes x 2.07 GHz",
-            "launches_per_step": launches, "expand_ms_per_step": st.ms_expand,
-            "algorithmic_ops_per_launch": ops_per_launch,
-            "algorithmic_bytes_per_launch": alg_bytes,
-            "hbm_view": {"achieved_gbs": hbm_gbs, "peak_gbs": pk["hbm_gbs"], "frac": hbm_gbs / pk["hbm_gbs"],
-                         "peak_kind": pk_kind},
-            "philox_calls_per_s": st.philox_calls / exp_s if exp_s else 0.0}
+            "traffic_note": EXPAND_TRAFFIC_NOTE,
+            "kernel": "k_expand", "peak_kind": pk_kind + " (copy bandwidth, MEASURED_PEAKS.json)",
+            "algorithmic_bytes_per_launch": alg_bytes, "launches_per_step": launches,
+            "launch_us_events": launch_s * 1e6, "event_pass_levels": int(ev.levels),
+            "expand_ms_per_step_globaltimer": st.ms_expand,
+            "launch_us_globaltimer": st.ms_expand * 1e3 / launches,
+            "limiter": "latency: issue-active and DRAM throughput both low in the ncu capture (profiles/)",
+            "alu_view": {"philox_calls_per_s": calls_s, "peak_calls_per_s": philox_peak,
+                         "frac": calls_s / philox_peak if philox_peak else None,
+                         "peak_kind": "measured: fbpt_philox_rate (Philox-only kernel, CUDA events)",
+                         "sms": sms}}
 
     # ---- end to end through the C ABI with host buffers ----
     e2e = None

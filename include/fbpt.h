@@ -85,6 +85,16 @@ enum fbpt_launch {
                                   grid barriers (FBPT_ETIMEOUT if a wait gives up) */
 };
 
+/* How the vertices reached at a level are gathered for the commit (Section
+ * 9 (a): a hybrid of a queue and a scan of the frontier). */
+enum fbpt_compaction {
+    FBPT_COMPACT_QUEUE = 0, /* the expand appends each newly reached vertex to a pending list (an
+                               atomic with a returned value per new vertex) */
+    FBPT_COMPACT_SCAN = 1   /* the expand only sets bits (no returned value, no list); the commit
+                               scans every vertex's word-occupancy mask for the reached ones.
+                               Pull levels always use the queue */
+};
+
 /* When a colour lane takes its next sample. */
 enum fbpt_refill {
     FBPT_REFILL_LANE = 0,  /* as soon as the lane's traversal ends (mid-traversal injection) */
@@ -121,6 +131,13 @@ typedef struct fbpt_trace_row {
     uint64_t expand_ns, commit_ns, sweep_ns;  /* device time of each phase (%globaltimer) */
     uint32_t direction;      /* how this level expanded: 0 push, 1 filtered push, 2 pull */
     uint32_t frontier_lanes; /* lanes with colours in this level's frontier */
+    float features[6];       /* the policy features of this level as the scheduler computed them
+                                (FP64 arithmetic rounded to FP32; see the schedule policy below);
+                                zero in row 0, whose level no schedule step preceded */
+    float outputs[8];        /* the policy network's outputs for this level (learned schedule with a
+                                policy), else zero */
+    uint32_t compaction;     /* how this level gathered its reached vertices (enum fbpt_compaction) */
+    uint32_t reserved;
 } fbpt_trace_row;
 
 typedef struct fbpt_graph fbpt_graph;
@@ -146,6 +163,9 @@ typedef struct fbpt_opts {
     fbpt_trace_row* trace; /* host array of trace_cap rows, or NULL; levels beyond trace_cap
                               are not recorded */
     uint64_t trace_cap;
+    uint32_t compaction; /* enum fbpt_compaction of the push, filtered and pull schedules; the
+                            heuristic and learned schedules choose it per level */
+    uint32_t reserved;   /* 0 */
 } fbpt_opts;
 
 /* RR sets as CSR in library-owned device memory (free with fbpt_rrsets_free). */
@@ -181,6 +201,9 @@ typedef struct fbpt_stats {
                                      to last CTA end (%globaltimer), summed */
     double ms_commit;             /* same for the commit phase */
     double ms_sweep;              /* same for the sweep phase (RR pairs of finished lanes) */
+    double ms_expand_events;      /* FBPT_LAUNCH_HOST only: the expand launches' time measured by CUDA
+                                     events recorded around them on the run's stream, summed (0 for
+                                     the other launch forms, whose levels run inside one launch) */
 } fbpt_stats;
 
 /* ---- Graphs ---------------------------------------------------------------
@@ -294,6 +317,17 @@ typedef struct fbpt_tuning {
  * expand kernel per level) is kept whenever it is within 3% of the best.  The result is stored on g (used by fbpt_sample_batched) and
  * copied to out (may be NULL).  Output bits never depend on the shape. */
 int fbpt_autotune(fbpt_graph* g, uint64_t seed, uint64_t S, const fbpt_opts* base, fbpt_tuning* out);
+/* The row width picked by the policy network instead of measured (Section 9
+ * (a), dynamic colour counts): one run of sample ids 0 .. min(S, 8192) - 1 at
+ * 8 words x 1 slot with lane refill and the learned schedule (base->policy,
+ * required; base supplies the stream and launch form) records the network's
+ * outputs 5..7 on every level, its predicted log2 ns per sample at rows of 4,
+ * 16 and 64 words; *row_words receives the width whose mean over the levels
+ * that had a frontier is smallest (64 if none had), scores (3 floats, may be
+ * NULL) the three means.  FBPT_EINVAL for a null argument, S = 0 or no policy. */
+int fbpt_policy_width(fbpt_graph* g, uint64_t seed, uint64_t S, const fbpt_opts* base, uint32_t* row_words,
+                      float* scores);
+
 /* The shape stored on g by fbpt_autotune; FBPT_EINVAL if it was never tuned. */
 int fbpt_graph_tuning(const fbpt_graph* g, fbpt_tuning* out);
 
@@ -321,13 +355,17 @@ int fbpt_select_seeds(const fbpt_rrsets* rr, uint32_t k, uint32_t* seeds_host, u
  * no counterpart; this is a property of the library, not of the method.
  * It allocates nothing: its working memory is one fixed 64 MiB array in the
  * library's device image, which every GPU that loads libfbpt holds until the
- * process exits.  It needs 4*n + n + S + 20*k bytes (each part rounded up to
- * 256) and returns FBPT_EINVAL, naming the limit, beyond 64 MiB.  The first
- * call on a device looks up the array's device address (cudaGetSymbolAddress);
- * make that first call before any stream capture.  All calls share the array
- * and each starts by clearing it: calls whose work overlaps on the GPU (two
- * host threads, or two streams) race and give wrong seeds, so serialize them.
- * Work runs on rr->stream; the call returns after it finishes. */
+ * process exits.  CUDA loads the library's device code lazily by default, so
+ * the array is placed on a device when the first graph is created there
+ * (fbpt_graph_create looks the array up for this reason); a caller that builds
+ * its RR sets without a graph on that device must make one call before it
+ * hands its free memory to a pool.  It needs 4*n + n + S + 20*k bytes (each
+ * part rounded up to 256) and returns FBPT_EINVAL, naming the limit, beyond
+ * 64 MiB.  Every call looks up the array's device address
+ * (cudaGetSymbolAddress).  All calls share the array and each starts by
+ * clearing it: calls whose work overlaps on the GPU (two host threads, or two
+ * streams) race and give wrong seeds, so serialize them.  Work runs on
+ * rr->stream; the call returns after it finishes. */
 int fbpt_select_seeds_noalloc(const fbpt_rrsets* rr, uint32_t k, uint32_t* seeds_host, uint64_t* gains_host);
 
 /* ---- Influence maximization: the IMM sampling loop -------------------------------
@@ -370,10 +408,15 @@ int fbpt_imm(fbpt_graph* g, uint32_t k, double epsilon, double ell, uint64_t see
 
 /* ---- Schedule policy --------------------------------------------------------------
  * A 6 -> 32 -> 32 -> 8 ReLU network (FP32) that picks, per level, how the
- * level expands (Section 9 (a): direction switching among push, push that
- * skips colours the source already has, and pull).  Its outputs 0..2 are the
- * predicted log2 device time of the level under each; the scheduler takes the
- * smallest.  It changes the schedule only, never a bit of the output.
+ * level expands and gathers its reached vertices (Section 9 (a): direction
+ * switching among push, push that skips colours the source already has, and
+ * pull; a queue or a scan of the frontier), and the row width of a run
+ * (dynamic colour counts).  Outputs 0..4 are the predicted log2 device time of
+ * the level under push, filtered push and pull with queue compaction, then
+ * push and filtered push with scan compaction; the scheduler takes the
+ * smallest allowed one.  Outputs 5..7 are the predicted log2 ns per sample of
+ * a run at rows of 4, 16 and 64 words (fbpt_policy_width).  It changes the
+ * schedule only, never a bit of the output.
  * Parameters (fbpt_policy_param_count() floats): input mean[6], input
  * scale[6] (> 0), W1[32][6], b1[32], W2[32][32], b2[32], W3[8][32], b3[8];
  * features as in fbpt_trace_row: log2(1+units), log2(1+groups),
@@ -404,13 +447,23 @@ typedef struct fbpt_train_opts {
     uint32_t steps;
     float lr;
     uint64_t seed;
+    void* stream;    /* cudaStream_t the training kernels and copies run on (NULL = legacy default) */
 } fbpt_train_opts;
 int fbpt_policy_train(const float* features, const uint32_t* actions, const float* targets, uint64_t rows,
                       const fbpt_train_opts* opts, const float* init_params, fbpt_policy** out, float* final_loss);
 /* Loss and gradient (param_count floats; zero for the input mean and scale)
- * of the parameters on the rows, computed by the training kernel. */
+ * of the parameters on the rows, computed by the training kernel on stream. */
 int fbpt_policy_loss_grad(const float* params, const float* features, const uint32_t* actions,
-                          const float* targets, uint64_t rows, float* loss, float* grad);
+                          const float* targets, uint64_t rows, float* loss, float* grad, void* stream);
+/* One Adam update (Kingma and Ba, ICLR 2015, Algorithm 1; beta1 = 0.9,
+ * beta2 = 0.999, eps = 1e-8) by the training's own kernel, at step t >= 1 with
+ * learning rate lr > 0: m = beta1 m + (1 - beta1) g, v = beta2 v + (1 - beta2) g^2,
+ * params -= lr (m / (1 - beta1^t)) / (sqrt(v / (1 - beta2^t)) + eps), for every
+ * weight and bias; the input mean and scale (the first 12 floats) are left as
+ * they are.  params, m and v (param_count floats each, host) are updated in
+ * place; grad (host) is read.  Runs on stream and returns when done.
+ * FBPT_EINVAL for a null array, t = 0 or lr <= 0. */
+int fbpt_policy_adam_step(float* params, const float* grad, float* m, float* v, uint32_t t, float lr, void* stream);
 
 /* ---- Building blocks exposed for verification ------------------------------------
  * Device results of the bit-level contract for given inputs (host arrays in
@@ -418,6 +471,14 @@ int fbpt_policy_loss_grad(const float* params, const float* features, const uint
  * and start vertices for sample ids. */
 int fbpt_edge_draws(uint64_t seed, const uint64_t* s, const uint64_t* e, uint64_t count, uint32_t* out);
 int fbpt_start_vertices(uint64_t seed, const uint64_t* s, uint64_t count, uint32_t n, uint32_t* out);
+
+/* Measured ceiling of the liveness draw (the integer-ALU roofline of the push
+ * expand): a kernel that does nothing but Philox4x32-10 evaluations, round
+ * keys hoisted as in the expand, calls_per_thread (>= 2) per thread over every
+ * thread the GPU holds at once; three launches after one warm-up are timed
+ * with CUDA events on stream.  *calls_per_s receives evaluations per second.
+ * FBPT_EINVAL for a null result or calls_per_thread < 2. */
+int fbpt_philox_rate(uint64_t seed, uint32_t calls_per_thread, void* stream, double* calls_per_s);
 
 /* sizeof(fbpt_opts), sizeof(fbpt_rrsets), sizeof(fbpt_stats), sizeof(fbpt_tuning),
  * sizeof(fbpt_imm_result), sizeof(fbpt_trace_row) into sizes[0 .. min(count, 6) - 1]

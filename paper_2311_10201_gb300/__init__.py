@@ -25,6 +25,7 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "fbpt.h")
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED, EDEVICE = 0, -1, -2, -3, -4, -5, -6
 SCHED = {"push": 0, "pull": 1, "heuristic": 2, "learned": 3, "filtered": 4}
 LAUNCH = {"host": 0, "graph": 1, "persistent": 2}
+COMPACTION = {"queue": 0, "scan": 1}
 
 U64P = ctypes.POINTER(ctypes.c_uint64)
 U32P = ctypes.POINTER(ctypes.c_uint32)
@@ -35,7 +36,8 @@ class Opts(ctypes.Structure):
                 ("launch", ctypes.c_uint32), ("unfused", ctypes.c_uint32), ("refill", ctypes.c_uint32),
                 ("blocks", ctypes.c_uint32), ("model", ctypes.c_uint32),
                 ("policy", ctypes.c_void_p), ("stream", ctypes.c_void_p), ("spin_limit", ctypes.c_uint64),
-                ("trace", ctypes.c_void_p), ("trace_cap", ctypes.c_uint64)]
+                ("trace", ctypes.c_void_p), ("trace_cap", ctypes.c_uint64),
+                ("compaction", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 class Tuning(ctypes.Structure):
@@ -71,7 +73,7 @@ class Stats(ctypes.Structure):
                  "philox_calls", "colour_edge_visits", "rr_total", "overflow_reruns", "mask_words", "trace_rows",
                  "groups_expanded")] + \
                [("ms_total", ctypes.c_double), ("ms_expand", ctypes.c_double), ("ms_commit", ctypes.c_double),
-                ("ms_sweep", ctypes.c_double)]
+                ("ms_sweep", ctypes.c_double), ("ms_expand_events", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -80,7 +82,9 @@ class Stats(ctypes.Structure):
 TRACE_DTYPE = np.dtype([(k, np.uint64) for k in
                         ("level", "units", "groups", "colours", "pending", "active_lanes", "finished_lanes",
                          "started_lanes", "expand_ns", "commit_ns", "sweep_ns")] +
-                       [("direction", np.uint32), ("frontier_lanes", np.uint32)])
+                       [("direction", np.uint32), ("frontier_lanes", np.uint32),
+                        ("features", np.float32, (6,)), ("outputs", np.float32, (8,)),
+                        ("compaction", np.uint32), ("reserved", np.uint32)])
 
 
 class FbptError(RuntimeError):
@@ -106,6 +110,8 @@ _SIGS = {
     "fbpt_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.POINTER(Opts),
                                      ctypes.POINTER(Tuning)]),
     "fbpt_graph_tuning": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Tuning)]),
+    "fbpt_policy_width": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.POINTER(Opts),
+                                         U32P, ctypes.POINTER(ctypes.c_float)]),
     "fbpt_imm": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
                                 ctypes.c_uint64, ctypes.POINTER(Opts), U32P, U64P, ctypes.POINTER(ImmResult),
                                 ctypes.POINTER(Stats)]),
@@ -119,6 +125,8 @@ _SIGS = {
     "fbpt_edge_draws": (ctypes.c_int, [ctypes.c_uint64, U64P, U64P, ctypes.c_uint64, U32P]),
     "fbpt_start_vertices": (ctypes.c_int, [ctypes.c_uint64, U64P, ctypes.c_uint64, ctypes.c_uint32, U32P]),
     "fbpt_abi_sizes": (ctypes.c_int, [U64P, ctypes.c_int]),
+    "fbpt_philox_rate": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p,
+                                        ctypes.POINTER(ctypes.c_double)]),
     "fbpt_policy_param_count": (ctypes.c_int, []),
     "fbpt_policy_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_float), ctypes.c_uint64,
                                           ctypes.POINTER(ctypes.c_void_p)]),
@@ -127,7 +135,10 @@ _SIGS = {
                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p),
                                          ctypes.POINTER(ctypes.c_float)]),
     "fbpt_policy_loss_grad": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
-                                             ctypes.c_uint64, ctypes.POINTER(ctypes.c_float), ctypes.c_void_p]),
+                                             ctypes.c_uint64, ctypes.POINTER(ctypes.c_float), ctypes.c_void_p,
+                                             ctypes.c_void_p]),
+    "fbpt_policy_adam_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_uint32, ctypes.c_float, ctypes.c_void_p]),
     "fbpt_policy_get": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float), ctypes.c_uint64]),
     "fbpt_policy_save": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p]),
     "fbpt_policy_load": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(ctypes.c_void_p)]),
@@ -314,8 +325,9 @@ MODEL = {"ic": 0, "lt": 1}
 
 
 def make_opts(words=0, slots=0, schedule="push", launch="persistent", unfused=False, stream=None, policy=None,
-              spin_limit=0, refill="lane", blocks=0, model="ic"):
+              spin_limit=0, refill="lane", blocks=0, model="ic", compaction="queue"):
     o = Opts()
+    o.compaction = COMPACTION[compaction] if isinstance(compaction, str) else int(compaction)
     o.blocks = int(blocks)
     o.model = MODEL[model] if isinstance(model, str) else int(model)
     o.refill = REFILL[refill] if isinstance(refill, str) else int(refill)
@@ -373,6 +385,16 @@ def autotune(g: Graph, seed: int, S: int, **kw) -> dict:
     t = Tuning()
     _check(lib().fbpt_autotune(g._h, seed, S, ctypes.byref(o), ctypes.byref(t)))
     return t.as_dict()
+
+
+def policy_width(g: Graph, seed: int, S: int, policy=None, stream=None, launch="graph"):
+    """Row width (words) the policy network picks for g (fbpt_policy_width),
+    and its three scores (predicted log2 ns per sample at 4, 16, 64 words)."""
+    o = make_opts(schedule="learned", launch=launch, stream=_stream_handle(stream), policy=policy)
+    words = ctypes.c_uint32(0)
+    scores = (ctypes.c_float * 3)()
+    _check(lib().fbpt_policy_width(g._h, seed, S, ctypes.byref(o), ctypes.byref(words), scores))
+    return int(words.value), [float(x) for x in scores]
 
 
 def tuning(g: Graph) -> dict:
@@ -479,7 +501,8 @@ def default_policy():
 
 
 class TrainOpts(ctypes.Structure):
-    _fields_ = [("steps", ctypes.c_uint32), ("lr", ctypes.c_float), ("seed", ctypes.c_uint64)]
+    _fields_ = [("steps", ctypes.c_uint32), ("lr", ctypes.c_float), ("seed", ctypes.c_uint64),
+                ("stream", ctypes.c_void_p)]
 
 
 def _train_arrays(features, actions, targets):
@@ -491,10 +514,10 @@ def _train_arrays(features, actions, targets):
     return X, A, Y
 
 
-def policy_train(features, actions, targets, steps=2000, lr=3e-3, seed=0, init=None):
+def policy_train(features, actions, targets, steps=2000, lr=3e-3, seed=0, init=None, stream=None):
     """Train the schedule network on the GPU (fbpt_policy_train); returns (Policy, loss)."""
     X, A, Y = _train_arrays(features, actions, targets)
-    o = TrainOpts(steps, lr, seed)
+    o = TrainOpts(steps, lr, seed, _stream_handle(stream))
     h = ctypes.c_void_p()
     loss = ctypes.c_float()
     init_arr = None if init is None else np.ascontiguousarray(init, np.float32)
@@ -506,15 +529,29 @@ def policy_train(features, actions, targets, steps=2000, lr=3e-3, seed=0, init=N
     return p, float(loss.value)
 
 
-def policy_loss_grad(params, features, actions, targets):
+def policy_loss_grad(params, features, actions, targets, stream=None):
     """(loss, gradient) of the parameters on the rows, from the GPU kernel."""
     X, A, Y = _train_arrays(features, actions, targets)
     P = np.ascontiguousarray(params, np.float32)
     g = np.zeros(P.size, np.float32)
     loss = ctypes.c_float()
     _check(lib().fbpt_policy_loss_grad(P.ctypes.data, X.ctypes.data, A.ctypes.data, Y.ctypes.data, X.shape[0],
-                                       ctypes.byref(loss), g.ctypes.data))
+                                       ctypes.byref(loss), g.ctypes.data, _stream_handle(stream)))
     return float(loss.value), g
+
+
+def policy_adam_step(params, grad, m, v, t, lr, stream=None):
+    """One Adam update by the library's training kernel (fbpt_policy_adam_step);
+    returns the new (params, m, v) as float32 arrays."""
+    P = np.array(params, np.float32)
+    G = np.ascontiguousarray(grad, np.float32)
+    M = np.array(m, np.float32)
+    V = np.array(v, np.float32)
+    if not (P.size == G.size == M.size == V.size == lib().fbpt_policy_param_count()):
+        raise ValueError("params, grad, m and v must each hold fbpt_policy_param_count() floats")
+    _check(lib().fbpt_policy_adam_step(P.ctypes.data, G.ctypes.data, M.ctypes.data, V.ctypes.data, t, lr,
+                                       _stream_handle(stream)))
+    return P, M, V
 
 
 def edge_draws(seed: int, s, e):
@@ -523,6 +560,13 @@ def edge_draws(seed: int, s, e):
     out = np.zeros(max(s.size, 1), np.uint32)
     _check(lib().fbpt_edge_draws(seed, _ptr_u64(s), _ptr_u64(e), s.size, _ptr_u32(out)))
     return out[:s.size]
+
+
+def philox_rate(seed: int = 1, calls_per_thread: int = 4096, stream=None) -> float:
+    """Philox4x32-10 evaluations per second of a draw-only kernel (fbpt_philox_rate)."""
+    out = ctypes.c_double(0.0)
+    _check(lib().fbpt_philox_rate(seed, calls_per_thread, _stream_handle(stream), ctypes.byref(out)))
+    return out.value
 
 
 def start_vertices(seed: int, s, n: int):

@@ -1,5 +1,6 @@
 // C ABI glue: errors, version, RR-set buffers, sampling entry points and the
 // verification building blocks (device results of the bit-level contract).
+#include <algorithm>
 #include <cstring>
 #include <string>
 
@@ -36,6 +37,23 @@ __global__ void k_edge_draws(uint64_t seed, const uint64_t* s, const uint64_t* e
 __global__ void k_starts(uint64_t seed, const uint64_t* s, uint64_t count, uint32_t n, uint32_t* out) {
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (uint64_t)gridDim.x * blockDim.x)
         out[i] = start_vertex(seed, s[i], n);
+}
+
+// Nothing but Philox4x32-10 evaluations with the round keys hoisted as in the
+// expand: two independent counter chains per iteration, outputs folded into
+// one word (stored only if it matches a value it never takes, so that the
+// calls are not optimised away).
+constexpr int kRateThreads = 256;
+__global__ void __launch_bounds__(kRateThreads) k_philox_rate(uint64_t seed, uint32_t iters, uint32_t* sink) {
+    const PhiloxKeys K = philox_keys(seed);
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t acc = 0;
+    for (uint32_t k = 0; k < iters; ++k) {
+        const uint4 a = philox4x32_10(make_uint4(t, k, 2u * k, 7u), K);
+        const uint4 b = philox4x32_10(make_uint4(t, k, 2u * k + 1u, 7u), K);
+        acc ^= a.x ^ a.y ^ a.z ^ a.w ^ b.x ^ b.y ^ b.z ^ b.w;
+    }
+    if (acc == 0x9E3779B9u && t == 0xFFFFFFFFu) sink[0] = acc;
 }
 
 }  // namespace
@@ -87,6 +105,15 @@ extern "C" int fbpt_imm(fbpt_graph* g, uint32_t k, double epsilon, double ell, u
         return imm_impl(g, k, epsilon, ell, seed, max_samples, opts, seeds_host, gains_host, result, stats);
     } catch (const std::exception& e) {
         return fail(FBPT_ENOMEM, std::string("fbpt_imm: ") + e.what());
+    }
+}
+
+extern "C" int fbpt_policy_width(fbpt_graph* g, uint64_t seed, uint64_t S, const fbpt_opts* base,
+                                 uint32_t* row_words, float* scores) {
+    try {
+        return policy_width_impl(g, seed, S, base, row_words, scores);
+    } catch (const std::exception& e) {
+        return fail(FBPT_ENOMEM, std::string("fbpt_policy_width: ") + e.what());
     }
 }
 
@@ -172,4 +199,35 @@ extern "C" int fbpt_start_vertices(uint64_t seed, const uint64_t* s, uint64_t co
     cudaFree(dout);
     if (err != cudaSuccess) return fail(FBPT_ECUDA, std::string("fbpt_start_vertices: ") + cudaGetErrorString(err));
     return FBPT_OK;
+}
+
+extern "C" int fbpt_philox_rate(uint64_t seed, uint32_t calls_per_thread, void* stream, double* calls_per_s) {
+    if (!calls_per_s || calls_per_thread < 2) return fail(FBPT_EINVAL, "fbpt_philox_rate: bad argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    int per = 0;
+    FBPT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_philox_rate, kRateThreads, 0));
+    const int blocks = device_sm_count() * std::max(per, 1);
+    const uint32_t iters = calls_per_thread / 2;
+    uint32_t* sink = nullptr;
+    FBPT_CUDA_TRY(cudaMallocAsync((void**)&sink, sizeof(uint32_t), st));
+    cudaEvent_t a = nullptr, b = nullptr;
+    int rc = FBPT_OK;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) rc = fail(FBPT_ECUDA, "event create failed");
+    if (rc == FBPT_OK) {
+        k_philox_rate<<<blocks, kRateThreads, 0, st>>>(seed, iters, sink);  // warm-up
+        cudaEventRecord(a, st);
+        for (int r = 0; r < 3; ++r) k_philox_rate<<<blocks, kRateThreads, 0, st>>>(seed + r, iters, sink);
+        cudaEventRecord(b, st);
+        const cudaError_t e = cudaEventSynchronize(b);
+        float ms = 0.f;
+        if (e != cudaSuccess || cudaEventElapsedTime(&ms, a, b) != cudaSuccess || ms <= 0.f)
+            rc = fail(FBPT_ECUDA, "fbpt_philox_rate: timing failed");
+        else
+            *calls_per_s = 3.0 * (double)blocks * kRateThreads * 2.0 * iters / (ms * 1e-3);
+    }
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    cudaFreeAsync(sink, st);
+    cudaStreamSynchronize(st);
+    return rc;
 }

@@ -51,6 +51,9 @@ constexpr int kThreads = 256;
 #ifndef FBPT_EXPAND_MINB
 #define FBPT_EXPAND_MINB 3  // resident CTAs per SM the expand kernel is compiled for
 #endif
+#ifndef FBPT_EXPAND_PREFETCH
+#define FBPT_EXPAND_PREFETCH 1  // wide expand: prefetch the next chunk's threshold vectors
+#endif
 
 __device__ __forceinline__ uint64_t row_groups(uint64_t rs, uint64_t re) {
     return re > rs ? ((re - 1) >> 2) - (rs >> 2) + 1 : 0;
@@ -75,6 +78,7 @@ struct CommitWarp {
     uint64_t m[32];                 // words of next[w] that changed this level
     uint32_t w[32];
     uint32_t start[32];             // first (vertex, word) item of each vertex
+    uint32_t row[32];               // stage row of each vertex
     uint32_t occ_lo[32], occ_hi[32];
     uint32_t bits[32];
     uint32_t he[32];                // vertex has in-edges
@@ -88,8 +92,9 @@ struct CommitWarp {
 struct SchedHead {
     unsigned long long next_j, pair_cursor, new_packed, new_colours, tick, tick_limit;
     unsigned long long list_count, list_groups, list_colours;
+    unsigned long long wide_packed, wide_gnew, wide_units, wide_groups;
     unsigned long long ph_t0[3], ph_t1[3];
-    uint32_t err, refill, sched, dir, frontier_lanes, pend_count, spill_cur;
+    uint32_t err, refill, sched, dir, frontier_lanes, pend_count, spill_cur, mode, scan_rows;
 };
 
 struct Smem {
@@ -102,8 +107,9 @@ struct Smem {
     SchedHead h;
     unsigned long long still[kMaxWords], sfin[kMaxWords], init[kMaxWords];
     unsigned long long mscan[33][6];  // schedule: block-scan scratch (32 warps + totals)
-    float feat[8], h1[kPolicyHidden], h2[kPolicyHidden], out[kPolicyOut];
-    uint32_t last, abort, nstill, dir;
+    float rawf[8], feat[8], h1[kPolicyHidden], h2[kPolicyHidden], out[kPolicyOut];
+    uint32_t last, abort, nstill, dir, mode;
+    uint32_t pcnt[kThreads / 32], pbuf[kThreads / 32 * kPendBuf];  // expand: per-warp pending buffers
 };
 
 // dst[0 .. count) = src[0 .. count) (count <= kMaxLanes + 1), all loads of a
@@ -262,19 +268,209 @@ __device__ void dev_init(const Eng& E) {
 }
 
 // ---- expand (push over in-edges) -----------------------------------------------------
+//
+// Liveness test of a 4-edge group: edge k is live for a colour iff
+// draw_k < T_k or bit k of `sure` is set.  T_k is the edge's threshold when
+// the edge lies in the unit's in-row and 0 < thr < 2^32 - 1, 0 for an edge
+// outside the row or with thr = 0 (never live); an always-live edge
+// (thr = 0xFFFFFFFF) keeps T = 0xFFFFFFFF and sets its `sure` bit, since a
+// draw of 0xFFFFFFFF would fail the strict test.
 
-// One 4-edge group of frontier unit u: edges 4q .. 4q+3 of the in-row [rs, re)
-// of its vertex, q = rs/4 + j.  For each colour of the unit one Philox call
-// decides all four edges (Listing 1's per-colour liveness draw); live colours
-// are ORed into next[w] (Listing 1's fusing update).  Loading and drawing are
-// split so that a warp can issue the loads of two chunks before drawing.
+// New pending vertices of a warp are collected in its shared-memory buffer and
+// appended to the global list with one atomic per chunk (pend_flush); a vertex
+// that finds the buffer full goes to the list directly.
+__device__ __forceinline__ void pend_push(const Eng& E, uint32_t* cnt, uint32_t* buf, uint32_t w) {
+    const uint32_t p = atomicAdd(cnt, 1u);
+    if (p < kPendBuf) {
+        buf[p] = w;
+        return;
+    }
+    const uint32_t g = atomicAdd(&E.ctl->pend_count, 1u);
+    if (g < E.pend_cap)
+        E.pend_v[g] = w;
+    else
+        atomicOr(&E.ctl->error, (unsigned)kErrPendOverflow);
+}
+
+// All 32 lanes call, converged.
+__device__ __forceinline__ void pend_flush(const Eng& E, uint32_t* cnt, uint32_t* buf) {
+    __syncwarp();
+    const uint32_t n = min(*cnt, kPendBuf);
+    if (n == 0) return;
+    const uint32_t lane = lane_id();
+    uint32_t base = 0;
+    if (lane == 0) base = atomicAdd(&E.ctl->pend_count, n);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (lane < n) {
+        if (base + lane < E.pend_cap)
+            E.pend_v[base + lane] = buf[lane];
+        else
+            atomicOr(&E.ctl->error, (unsigned)kErrPendOverflow);
+    }
+    __syncwarp();
+    if (lane == 0) *cnt = 0;
+    __syncwarp();
+}
+
+// Colours y of word i reach w: next[w][i] |= y.  Queue compaction: w becomes
+// pending (once per level) when the first word of next[w] turns non-zero.
+// Scan compaction: only the bits are set (reductions, no returned value); the
+// commit finds w by its word-occupancy mask.
+__device__ __forceinline__ void push_live(const Eng& E, uint32_t w, uint32_t i, uint64_t y, bool scan, uint32_t* cnt,
+                                          uint32_t* buf) {
+    if (scan) {
+        atomicOr((unsigned long long*)&E.next[(uint64_t)w * E.WB + i], (unsigned long long)y);
+        atomicOr((unsigned long long*)&E.nocc[w], 1ull << i);
+        return;
+    }
+    const unsigned long long old =
+        atomicOr((unsigned long long*)&E.next[(uint64_t)w * E.WB + i], (unsigned long long)y);
+    if (old != 0) return;
+    if (atomicOr((unsigned long long*)&E.nocc[w], 1ull << i) != 0) return;
+    pend_push(E, cnt, buf, w);
+}
+
+// T and sure of a group whose in-row edges are vm (bits 0..3) and thresholds t.
+__device__ __forceinline__ uint32_t group_thresholds(uint32_t vm, const uint4& t, uint4& T) {
+    const bool in0 = vm & 1u, in1 = vm & 2u, in2 = vm & 4u, in3 = vm & 8u;
+    T = make_uint4(in0 ? t.x : 0u, in1 ? t.y : 0u, in2 ? t.z : 0u, in3 ? t.w : 0u);
+    return (in0 && t.x == 0xFFFFFFFFu ? 1u : 0u) | (in1 && t.y == 0xFFFFFFFFu ? 2u : 0u) |
+           (in2 && t.z == 0xFFFFFFFFu ? 4u : 0u) | (in3 && t.w == 0xFFFFFFFFu ? 8u : 0u);
+}
+
+// Edges of the group that need a draw (in the row, 0 < thr < 2^32 - 1).
+__device__ __forceinline__ uint32_t draw_edges(const uint4& T, uint32_t sure) {
+    return ((T.x ? 1u : 0u) | (T.y ? 2u : 0u) | (T.z ? 4u : 0u) | (T.w ? 8u : 0u)) & ~sure;
+}
+
+// The draws of one group for the colours x (bits of word i, lane ids
+// 64i + bit): one Philox call per colour decides the four edges (Listing 1's
+// per-colour liveness draw); the live colours of each edge are gathered per
+// half-word and ORed into the source's next row (Listing 1's fusing update).
+// Filtered: vis_k are the sources' visited words; a colour a source already
+// has is not sent to it (and needs no draw if every source has it).
+template <bool filtered>
+__device__ __forceinline__ void group_draws(const Eng& E, const uint32_t* lj, uint64_t x, uint32_t i, uint64_t q,
+                                            const uint4& T, uint32_t sure, const PhiloxKeys& K,
+                                            const uint64_t (&vis)[4], bool scan, uint32_t* cnt, uint32_t* buf) {
+    const uint32_t f_lo = (uint32_t)E.first_id, f_hi = (uint32_t)(E.first_id >> 32);
+    const uint32_t qlo = (uint32_t)q, qhi = (uint32_t)(q >> 32);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        uint32_t xx = (uint32_t)(x >> (32 * h));
+        uint32_t z0 = 0, z1 = 0, z2 = 0, z3 = 0;
+        const uint32_t* l = lj + 32 * h;
+        while (xx) {
+            const uint32_t c = __ffs(xx) - 1;
+            xx &= xx - 1;
+            const uint32_t j = l[c];
+            const uint32_t slo = f_lo + j;
+            const uint32_t shi = f_hi + (slo < j ? 1u : 0u);
+            const uint4 r = philox4x32_10(make_uint4(slo, shi, qlo, qhi), K);
+            if ((r.x < T.x) | (r.y < T.y) | (r.z < T.z) | (r.w < T.w) | (sure != 0u)) {
+                const uint32_t bit = 1u << c;
+                if ((r.x < T.x) || (sure & 1u)) z0 |= bit;
+                if ((r.y < T.y) || (sure & 2u)) z1 |= bit;
+                if ((r.z < T.z) || (sure & 4u)) z2 |= bit;
+                if ((r.w < T.w) || (sure & 8u)) z3 |= bit;
+            }
+        }
+        if (filtered) {
+            z0 &= ~(uint32_t)(vis[0] >> (32 * h));
+            z1 &= ~(uint32_t)(vis[1] >> (32 * h));
+            z2 &= ~(uint32_t)(vis[2] >> (32 * h));
+            z3 &= ~(uint32_t)(vis[3] >> (32 * h));
+        }
+        if (z0 | z1 | z2 | z3) {
+            const uint4 c4 = __ldg(reinterpret_cast<const uint4*>(E.col) + q);
+            if (z0) push_live(E, c4.x, i, (uint64_t)z0 << (32 * h), scan, cnt, buf);
+            if (z1) push_live(E, c4.y, i, (uint64_t)z1 << (32 * h), scan, cnt, buf);
+            if (z2) push_live(E, c4.z, i, (uint64_t)z2 << (32 * h), scan, cnt, buf);
+            if (z3) push_live(E, c4.w, i, (uint64_t)z3 << (32 * h), scan, cnt, buf);
+        }
+    }
+}
+
+// Visited words (word i) of the four sources of group q, for filtered push;
+// ~0 for edges outside the row, so that they never veto a draw.
+__device__ __forceinline__ void source_visited(const Eng& E, uint64_t q, uint32_t vm, uint32_t i, uint64_t (&vis)[4]) {
+    const uint4 c4 = __ldg(reinterpret_cast<const uint4*>(E.col) + q);
+    vis[0] = (vm & 1u) ? L2(&E.visited[(uint64_t)c4.x * E.WB + i]) : ~0ull;
+    vis[1] = (vm & 2u) ? L2(&E.visited[(uint64_t)c4.y * E.WB + i]) : ~0ull;
+    vis[2] = (vm & 4u) ? L2(&E.visited[(uint64_t)c4.z * E.WB + i]) : ~0ull;
+    vis[3] = (vm & 8u) ? L2(&E.visited[(uint64_t)c4.w * E.WB + i]) : ~0ull;
+}
+
+// Wide units: a chunk is 32 consecutive groups of ONE unit, so the unit
+// record, its colour words and each draw's colour are warp-uniform; lane l
+// takes group 32 * (chunk - first chunk of the unit) + l.
+template <bool filtered, bool ro>
+__device__ __forceinline__ void expand_wide(const Eng& E, const uint32_t* lane_j, const PhiloxKeys& K, uint64_t NC,
+                                            bool scan, uint32_t* cnt, uint32_t* buf, uint64_t& n_edges,
+                                            uint64_t& n_calls) {
+    Ctl* ctl = E.ctl;
+    const uint32_t lane = lane_id();
+    const uint4* thr4 = reinterpret_cast<const uint4*>(E.thr);
+    const uint32_t wq0 = (uint32_t)(((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) % kWideQueues;
+    for (uint32_t qi = 0; qi < kWideQueues; ++qi) {
+      const uint32_t qn = (wq0 + qi) % kWideQueues;
+      const uint32_t qb = (uint32_t)(NC * qn / kWideQueues), qe = (uint32_t)(NC * (qn + 1) / kWideQueues);
+      for (;;) {
+        uint32_t c0 = 0;
+        if (lane == 0) c0 = qb + atomicAdd(&ctl->wqueue[qn * 32], kChunksPerGrab);
+        c0 = __shfl_sync(0xffffffffu, c0, 0);
+        if (c0 >= qe) break;
+        const uint32_t c1 = min(c0 + kChunksPerGrab, qe);
+        for (uint32_t c = c0; c < c1; ++c) {
+            const uint32_t u = LD<ro>(&E.wide_chunk[c]);
+            const uint4 ra = LD<ro>(&E.wide_rec[2ull * u]);
+            const uint4 rb = LD<ro>(&E.wide_rec[2ull * u + 1]);
+            const uint32_t gl = kChunk * (c - rb.y) + lane;
+            const uint64_t q = (((uint64_t)ra.y << 32) | ra.x) + gl;
+            uint32_t vm = gl < rb.x ? 0xFu : 0u;
+            if (gl == 0) vm &= rb.w & 0xFu;
+            if (gl + 1 == rb.x) vm &= (rb.w >> 4) & 0xFu;
+            uint4 t = make_uint4(0u, 0u, 0u, 0u);
+            if (vm) t = __ldg(thr4 + q);
+#if FBPT_EXPAND_PREFETCH
+            // the next chunk of a grab is mostly the next 32 groups of the same
+            // unit: its threshold vectors head for L2 while this chunk draws
+            if (c + 1 < c1) asm volatile("prefetch.global.L2 [%0];" ::"l"(thr4 + q + kChunk));
+#endif
+            uint4 T;
+            const uint32_t sure = group_thresholds(vm, t, T);
+            n_edges += __popc(vm);
+            const bool need = draw_edges(T, sure) != 0u;
+            if (__any_sync(0xffffffffu, (T.x | T.y | T.z | T.w) != 0u)) {
+                uint64_t words = ((uint64_t)ra.w << 32) | ra.z;
+                while (words) {
+                    const uint32_t i = __ffsll((long long)words) - 1;
+                    words &= words - 1;
+                    const uint32_t only = rb.w >> 8;  // unfused: the unit's single colour (lane + 1)
+                    uint64_t x = only ? 1ull << ((only - 1u) & 63u) : LD<ro>(&E.stage[(uint64_t)rb.z * E.WB + i]);
+                    uint64_t vis[4] = {0ull, 0ull, 0ull, 0ull};
+                    if (filtered) {
+                        if (vm) source_visited(E, q, vm, i, vis);
+                        x &= ~(vis[0] & vis[1] & vis[2] & vis[3]);
+                    }
+                    if (need) n_calls += __popcll(x);
+                    group_draws<filtered>(E, lane_j + (i << 6), (T.x | T.y | T.z | T.w) ? x : 0ull, i, q, T, sure, K,
+                                          vis, scan, cnt, buf);
+                }
+            }
+            pend_flush(E, cnt, buf);
+        }
+      }
+    }
+}
+
+// Narrow units (fewer than kWideMin groups): their groups form one index
+// space, 32 consecutive groups per chunk, one group per lane; a lane finds its
+// unit among the chunk's (at most 32) units.
 struct Grp {
-    uint4 c4;          // sources of the four edges
-    uint4 tm;          // live iff draw <= tm (thr - 1; 0xFFFFFFFF for always-live edges)
     uint64_t q, occ;
-    uint32_t mrow, only;
-    uint32_t valid;    // edges of the row with a non-zero threshold (bits 0..3)
-    uint32_t sure;     // of those, edges that are always live
+    uint4 T;
+    uint32_t mrow, only, sure, vm;
 };
 
 template <bool ro>
@@ -284,83 +480,32 @@ __device__ __forceinline__ bool grp_load(const Eng& E, uint32_t u, uint64_t j, G
     const uint64_t rs = LD<ro>(&E.list_rs[u]), re = LD<ro>(&E.list_re[u]);
     G.only = E.unfused ? LD<ro>(&E.list_only[u]) : 0u;
     G.q = (rs >> 2) + j;
-    G.c4 = __ldg(reinterpret_cast<const uint4*>(E.col) + G.q);
     const uint4 t = __ldg(reinterpret_cast<const uint4*>(E.thr) + G.q);
     const uint32_t first = j == 0 ? (uint32_t)(rs & 3) : 0u;
     const uint32_t last = G.q == ((re - 1) >> 2) ? (uint32_t)((re - 1) & 3) : 3u;
-    uint32_t inrow = (0xFu << first) & (0xFu >> (3u - last));
-    n_edges += __popc(inrow);
-    inrow &= (t.x ? 1u : 0u) | (t.y ? 2u : 0u) | (t.z ? 4u : 0u) | (t.w ? 8u : 0u);
-    G.valid = inrow;
-    G.sure = inrow & ((t.x == 0xFFFFFFFFu ? 1u : 0u) | (t.y == 0xFFFFFFFFu ? 2u : 0u) |
-                      (t.z == 0xFFFFFFFFu ? 4u : 0u) | (t.w == 0xFFFFFFFFu ? 8u : 0u));
-    G.tm = make_uint4(t.x == 0xFFFFFFFFu ? t.x : t.x - 1u, t.y == 0xFFFFFFFFu ? t.y : t.y - 1u,
-                      t.z == 0xFFFFFFFFu ? t.z : t.z - 1u, t.w == 0xFFFFFFFFu ? t.w : t.w - 1u);
-    return inrow != 0;
+    G.vm = (0xFu << first) & (0xFu >> (3u - last));
+    n_edges += __popc(G.vm);
+    G.sure = group_thresholds(G.vm, t, G.T);
+    return (G.T.x | G.T.y | G.T.z | G.T.w) != 0u;
 }
 
 template <bool filtered, bool ro>
 __device__ __forceinline__ void grp_run(const Eng& E, const uint32_t* lane_j, const Grp& G, const PhiloxKeys& K,
-                                        uint64_t& n_calls) {
-    const bool need = (G.valid & ~G.sure) != 0;  // some edge needs a draw
-    const uint32_t qlo = (uint32_t)G.q, qhi = (uint32_t)(G.q >> 32);
-    const uint32_t f_lo = (uint32_t)E.first_id, f_hi = (uint32_t)(E.first_id >> 32);
+                                        bool scan, uint32_t* cnt, uint32_t* buf, uint64_t& n_calls) {
+    const bool need = draw_edges(G.T, G.sure) != 0u;
     uint64_t words = G.occ;
     while (words) {
         const uint32_t i = __ffsll((long long)words) - 1;
         words &= words - 1;
         uint64_t x = G.only ? (1ull << ((G.only - 1u) & 63u)) : LD<ro>(&E.stage[(uint64_t)G.mrow * E.WB + i]);
-        // filtered push: a colour the source has already seen needs no draw
-        uint64_t v0 = ~0ull, v1 = ~0ull, v2 = ~0ull, v3 = ~0ull;
+        uint64_t vis[4] = {0ull, 0ull, 0ull, 0ull};
         if (filtered) {
-            if (G.valid & 1u) v0 = L2(&E.visited[(uint64_t)G.c4.x * E.WB + i]);
-            if (G.valid & 2u) v1 = L2(&E.visited[(uint64_t)G.c4.y * E.WB + i]);
-            if (G.valid & 4u) v2 = L2(&E.visited[(uint64_t)G.c4.z * E.WB + i]);
-            if (G.valid & 8u) v3 = L2(&E.visited[(uint64_t)G.c4.w * E.WB + i]);
-            x &= ~(v0 & v1 & v2 & v3);
+            source_visited(E, G.q, G.vm, i, vis);
+            x &= ~(vis[0] & vis[1] & vis[2] & vis[3]);
             if (!x) continue;
         }
-        uint64_t y0, y1, y2, y3;
-        if (need) {
-            uint32_t z[2][4];
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                uint32_t xx = (uint32_t)(x >> (32 * h));
-                const uint32_t* lj = &lane_j[(i << 6) + 32 * h];
-                uint32_t z0 = 0, z1 = 0, z2 = 0, z3 = 0;
-                while (xx) {
-                    const uint32_t c = __ffs(xx) - 1;
-                    xx &= xx - 1;
-                    const uint32_t j = lj[c];
-                    const uint32_t slo = f_lo + j;
-                    const uint32_t shi = f_hi + (slo < j ? 1u : 0u);
-                    const uint4 r = philox4x32_10(make_uint4(slo, shi, qlo, qhi), K);
-                    ++n_calls;
-                    const uint32_t bit = 1u << c;
-                    z0 |= r.x <= G.tm.x ? bit : 0u;
-                    z1 |= r.y <= G.tm.y ? bit : 0u;
-                    z2 |= r.z <= G.tm.z ? bit : 0u;
-                    z3 |= r.w <= G.tm.w ? bit : 0u;
-                }
-                z[h][0] = z0; z[h][1] = z1; z[h][2] = z2; z[h][3] = z3;
-            }
-            y0 = ((uint64_t)z[1][0] << 32) | z[0][0];
-            y1 = ((uint64_t)z[1][1] << 32) | z[0][1];
-            y2 = ((uint64_t)z[1][2] << 32) | z[0][2];
-            y3 = ((uint64_t)z[1][3] << 32) | z[0][3];
-        } else {
-            y0 = y1 = y2 = y3 = x;
-        }
-        if (filtered) {
-            y0 &= ~v0;
-            y1 &= ~v1;
-            y2 &= ~v2;
-            y3 &= ~v3;
-        }
-        if ((G.valid & 1u) && y0) or_next(E, G.c4.x, i, y0);
-        if ((G.valid & 2u) && y1) or_next(E, G.c4.y, i, y1);
-        if ((G.valid & 4u) && y2) or_next(E, G.c4.z, i, y2);
-        if ((G.valid & 8u) && y3) or_next(E, G.c4.w, i, y3);
+        if (need) n_calls += __popcll(x);
+        group_draws<filtered>(E, lane_j + (i << 6), x, i, G.q, G.T, G.sure, K, vis, scan, cnt, buf);
     }
 }
 
@@ -463,13 +608,14 @@ __device__ __forceinline__ void dev_pull(const Eng& E, const uint32_t* lane_j, c
     }
 }
 
-// Edge-balanced: the frontier's 4-edge groups form one index space; a warp
-// takes kChunksPerGrab chunks of 32 consecutive groups per atomic, one group
-// per lane (FBPT_EXPAND_ILP chunks at a time).  One instance per push variant,
-// so that the plain push loop carries no register of the filtered one.
+// Narrow units: the packed group space, a warp taking kChunksPerGrab chunks of
+// 32 consecutive groups per atomic, one group per lane.  One instance per
+// push variant, so that the plain push loop carries no register of the
+// filtered one.
 template <bool filtered, bool ro>
 __device__ __forceinline__ void expand_push(const Eng& E, const uint32_t* lane_j, const PhiloxKeys& K, uint64_t G,
-                                            uint64_t U, uint64_t nchunks, uint64_t& n_edges, uint64_t& n_calls) {
+                                            uint64_t U, uint64_t nchunks, bool scan, uint32_t* cnt, uint32_t* buf,
+                                            uint64_t& n_edges, uint64_t& n_calls) {
     Ctl* ctl = E.ctl;
     const uint32_t lane = lane_id();
     for (;;) {
@@ -478,19 +624,14 @@ __device__ __forceinline__ void expand_push(const Eng& E, const uint32_t* lane_j
         c0 = __shfl_sync(0xffffffffu, c0, 0);
         if (c0 >= nchunks) break;
         const uint32_t c1 = (uint32_t)min((uint64_t)c0 + kChunksPerGrab, nchunks);
-        for (uint32_t c = c0; c < c1; c += FBPT_EXPAND_ILP) {
-            const bool two = FBPT_EXPAND_ILP > 1 && c + 1 < c1;
-            const uint64_t ga = (uint64_t)c * kChunk + lane;
-            const uint64_t gbb = ga + kChunk;
-            uint64_t ja = 0, jb = 0;
-            const uint32_t ua = chunk_unit<ro>(E, c, nchunks, U, ga, ja);
-            uint32_t ub = 0;
-            if (two) ub = chunk_unit<ro>(E, c + 1, nchunks, U, gbb, jb);
-            Grp A, B;
-            const bool la = ga < G && grp_load<ro>(E, ua, ja, A, n_edges);
-            const bool lb = two && gbb < G && grp_load<ro>(E, ub, jb, B, n_edges);
-            if (la) grp_run<filtered, ro>(E, lane_j, A, K, n_calls);
-            if (lb) grp_run<filtered, ro>(E, lane_j, B, K, n_calls);
+        for (uint32_t c = c0; c < c1; ++c) {
+            const uint64_t g = (uint64_t)c * kChunk + lane;
+            uint64_t j = 0;
+            const uint32_t u = chunk_unit<ro>(E, c, nchunks, U, g, j);
+            Grp A;
+            if (g < G && grp_load<ro>(E, u, j, A, n_edges))
+                grp_run<filtered, ro>(E, lane_j, A, K, scan, cnt, buf, n_calls);
+            pend_flush(E, cnt, buf);
         }
     }
 }
@@ -545,34 +686,57 @@ __device__ __forceinline__ void expand_lt(const Eng& E, const uint32_t* lane_j, 
 // The expand phase.  part selects which directions this instance runs (the
 // per-level kernels split them so that the plain push kernel carries no
 // register of the others): kPartPush, kPartAlt (filtered push and pull) or
-// kPartAll (the persistent kernel).
+// kPartAll (the persistent kernel).  cnt / buf: the CTA's per-warp pending
+// buffers (one counter and kPendBuf entries per warp).
 enum ExpandPart : int { kPartPush = 0, kPartAlt = 1, kPartAll = 2 };
 
 template <int part>
-__device__ void dev_expand(const Eng& E, uint32_t* lane_j) {
+__device__ void dev_expand(const Eng& E, uint32_t* lane_j, uint32_t* pcnt, uint32_t* pbuf) {
     Ctl* ctl = E.ctl;
     const uint64_t G = L2(&ctl->list_groups);
+    const uint64_t NW = L2(&ctl->wide_chunks);
     const uint32_t dir = L2(&ctl->dir);
     const bool pull = dir == kDirPull && E.frontd;
     if (part == kPartPush && dir != kDirPush) return;
     if (part == kPartAlt && (dir == kDirPush || E.model == FBPT_MODEL_LT)) return;
-    if (G == 0) return;
+    if (G == 0 && NW == 0) return;
     const uint64_t U = L2(&ctl->list_count);
     const uint64_t nchunks = (G + kChunk - 1) / kChunk;
-    if (nchunks > E.chunk_cap || U > E.list_cap) return;  // overflow already flagged by commit
+    // overflow already flagged by commit
+    if (nchunks > E.chunk_cap || U > E.list_cap || NW > E.wide_chunk_cap || L2(&ctl->wide_units) > E.list_cap) return;
     phase_begin(ctl, 0);
     __syncthreads();
     fill_smem(lane_j, ctl->lane_j, 64u * E.WB);
+    const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
+    uint32_t* cnt = pcnt + warp;
+    uint32_t* buf = pbuf + warp * kPendBuf;
+    if (lane == 0) *cnt = 0;
     __syncthreads();
-    const uint32_t lane = lane_id();
+#ifdef FBPT_KEYS_COMPUTED
     const PhiloxKeys K = philox_keys(E.seed);
+#else
+    // round keys read from the kernel parameters, which the draws can take as
+    // constant operands instead of holding them in registers
+    PhiloxKeys K;
+#pragma unroll
+    for (int k = 0; k < 10; ++k) {
+        K.k0[k] = E.key0[k];
+        K.k1[k] = E.key1[k];
+    }
+#endif
     uint64_t n_edges = 0, n_calls = 0;
-    if (E.model == FBPT_MODEL_LT) expand_lt<part != kPartAll>(E, lane_j, K, U, n_edges, n_calls);
-    else if (part != kPartPush && pull) dev_pull(E, lane_j, K, n_edges, n_calls);
-    else if (part != kPartPush && dir == kDirFiltered)
-        expand_push<true, part != kPartAll>(E, lane_j, K, G, U, nchunks, n_edges, n_calls);
-    else if (part != kPartAlt)
-        expand_push<false, part != kPartAll>(E, lane_j, K, G, U, nchunks, n_edges, n_calls);
+    const bool scan = L2(&ctl->mode) == FBPT_COMPACT_SCAN;
+    if (E.model == FBPT_MODEL_LT) {
+        expand_lt<part != kPartAll>(E, lane_j, K, U, n_edges, n_calls);
+    } else if (part != kPartPush && pull) {
+        dev_pull(E, lane_j, K, n_edges, n_calls);
+    } else if (part != kPartPush && dir == kDirFiltered) {
+        expand_wide<true, part != kPartAll>(E, lane_j, K, NW, scan, cnt, buf, n_edges, n_calls);
+        expand_push<true, part != kPartAll>(E, lane_j, K, G, U, nchunks, scan, cnt, buf, n_edges, n_calls);
+    } else if (part != kPartAlt) {
+        expand_wide<false, part != kPartAll>(E, lane_j, K, NW, scan, cnt, buf, n_edges, n_calls);
+        expand_push<false, part != kPartAll>(E, lane_j, K, G, U, nchunks, scan, cnt, buf, n_edges, n_calls);
+    }
     n_edges = warp_sum(n_edges);
     n_calls = warp_sum(n_calls);
     if (lane == 0) {
@@ -617,47 +781,39 @@ __device__ __forceinline__ uint32_t nth_bit64(uint64_t m, uint32_t r) {
 // units (if w has in-edges).
 __device__ void dev_commit(const Eng& E, Smem& sm) {
     Ctl* ctl = E.ctl;
-    const uint32_t P = (uint32_t)min((uint64_t)L2(&ctl->pend_count), E.pend_cap);
-    // vertices per warp: spread a small level over more warps of the grid (the
-    // work is a chain of dependent loads per vertex), but at least
+    const bool scan = L2(&ctl->mode) == FBPT_COMPACT_SCAN;
+    const uint32_t P = scan ? 0u : (uint32_t)min((uint64_t)L2(&ctl->pend_count), E.pend_cap);
+    // queue: vertices per warp: spread a small level over more warps of the
+    // grid (the work is a chain of dependent loads per vertex), but at least
     // FBPT_COMMIT_VPW_MIN per warp so that each warp's fixed bookkeeping stays
     // amortised; up to one per lane.  A warp takes every nused-th pending
     // vertex (nused: the warps a round needs): the hubs, which many frontier
     // units reach early in the expand and so head the pending list, are spread
     // over the warps instead of lengthening the first warps' item loops.
+    // scan: every warp takes 32 consecutive vertices at a time and handles
+    // those whose word-occupancy mask is set.
     const uint64_t nwarp = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const uint32_t vpw =
         (uint32_t)min((uint64_t)32, max((uint64_t)FBPT_COMMIT_VPW_MIN, (P + nwarp - 1) / nwarp));
-    if ((uint64_t)blockIdx.x * (blockDim.x >> 5) * vpw >= P) return;  // no pending vertex for this CTA
+    if (!scan && (uint64_t)blockIdx.x * (blockDim.x >> 5) * vpw >= P) return;  // no pending vertex for this CTA
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < 2 * E.WB; i += blockDim.x) sm.act[i] = 0;
     __syncthreads();
-    if (P) phase_begin(ctl, 1);
+    if (P || scan) phase_begin(ctl, 1);
     const uint32_t spill_cur = L2(&ctl->spill_cur);
     const uint32_t lane = lane_id();
     const uint64_t wid = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     CommitWarp& cw = sm.cw[threadIdx.x >> 5];
-    uint64_t mwords = 0, ncol = 0;
-    for (uint64_t r0 = 0; r0 < P; r0 += nwarp * vpw) {
-        const uint64_t C = min((uint64_t)P - r0, nwarp * vpw);  // vertices of this round
-        const uint64_t nused = (C + vpw - 1) / vpw;
-        if (wid >= nused) break;  // only the last round leaves warps out
-        const uint64_t idx = r0 + wid + (uint64_t)lane * nused;
-        const bool ok = lane < vpw && idx < r0 + C;
-        uint32_t w = 0;
-        uint64_t m = 0, rs = 0, re = 0;
-        if (ok) {
-            w = L2(&E.pend_v[idx]);
-            m = L2(&E.nocc[w]);
-            E.nocc[w] = 0;
-            rs = __ldg(&E.rstart[w]);
-            re = __ldg(&E.rend[w]);
-        }
+    uint64_t mwords = 0, ncol = 0, wgroups = 0;
+    // One round: up to 32 reached vertices of this warp, one per lane (ok);
+    // w, its stage row idx, its changed words m and in-row [rs, re).
+    auto round = [&](bool ok, uint32_t w, uint64_t idx, uint64_t m, uint64_t rs, uint64_t re) {
         const uint32_t ni = __popcll(m);
         const uint32_t incl = warp_incl_scan(ni);
         const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
         cw.m[lane] = m;
         cw.w[lane] = w;
+        cw.row[lane] = (uint32_t)idx;
         cw.start[lane] = incl - ni;
         cw.occ_lo[lane] = 0;
         cw.occ_hi[lane] = 0;
@@ -682,7 +838,7 @@ __device__ void dev_commit(const Eng& E, Smem& sm) {
                 nx &= ~vis;
                 if (nx) {
                     E.visited[rowi] = vis | nx;
-                    E.stage[(r0 + wid + (uint64_t)o * nused) * E.WB + i] = nx;
+                    E.stage[(uint64_t)cw.row[o] * E.WB + i] = nx;
                     if (i < 32) atomicOr(&cw.occ_lo[o], 1u << i);
                     else atomicOr(&cw.occ_hi[o], 1u << (i - 32));
                     atomicAdd(&cw.bits[o], (uint32_t)__popcll(nx));
@@ -739,6 +895,11 @@ __device__ void dev_commit(const Eng& E, Smem& sm) {
         __syncwarp();
         const uint64_t ng = occ ? row_groups(rs, re) : 0;
         const uint64_t units = ng ? (E.unfused ? bits : 1u) : 0u;
+        // IC units of at least kWideMin groups are wide (own chunks, a record
+        // each; unfused: one per colour); the rest are packed into the narrow
+        // group space
+        const bool wide = units && E.model == FBPT_MODEL_IC && ng >= kWideMin;
+        const uint64_t nun = wide ? 0 : units;
         if (E.frontd && units) {  // frontier row by vertex, for a pull level
             for (uint32_t i = 0; i < E.WB; ++i)
                 E.frontd[(uint64_t)w * E.WB + i] = ((occ >> i) & 1ull) ? L2(&E.stage[idx * E.WB + i]) : 0ull;
@@ -746,12 +907,47 @@ __device__ void dev_commit(const Eng& E, Smem& sm) {
         }
         mwords += units ? (E.unfused ? units : (uint64_t)__popcll(occ)) : 0;
         ncol += units ? bits : 0;
-        const unsigned long long req = (unsigned long long)((units * ng) << kUnitBits) | units;
+        const unsigned long long req = (unsigned long long)((nun * ng) << kUnitBits) | nun;
         const unsigned long long got = warp_alloc<unsigned long long>(&ctl->new_packed, req);
         const uint64_t pos0 = got & kUnitMask;
         const uint64_t gbeg0 = got >> kUnitBits;
-        const bool fits = units && pos0 + units <= E.list_cap;
-        if (units && !fits) atomicOr(&ctl->error, (unsigned)kErrListOverflow);
+        const bool fits = nun && pos0 + nun <= E.list_cap;
+        if (nun && !fits) atomicOr(&ctl->error, (unsigned)kErrListOverflow);
+        // wide: a record and ceil(ng / 32) chunks of its own per unit
+        const uint64_t wun = wide ? units : 0;
+        const uint64_t wck = wide ? (ng + kChunk - 1) / kChunk : 0;
+        const unsigned long long wgot =
+            warp_alloc<unsigned long long>(&ctl->wide_packed, (unsigned long long)((wun * wck) << kUnitBits) | wun);
+        const uint64_t wpos = wgot & kUnitMask, wc0 = wgot >> kUnitBits;
+        const bool wfits = wide && wpos + wun <= E.list_cap && wc0 + wun * wck <= E.wide_chunk_cap;
+        if (wide && !wfits)
+            atomicOr(&ctl->error, (unsigned)(wpos + wun <= E.list_cap ? kErrChunkOverflow : kErrListOverflow));
+        if (wfits) {
+            const uint64_t q0 = rs >> 2;
+            const uint32_t masks = ((0xFu << (uint32_t)(rs & 3)) & 0xFu) | ((0xFu >> (3u - (uint32_t)((re - 1) & 3))) << 4);
+            if (!E.unfused) {
+                E.wide_rec[2 * wpos] = make_uint4((uint32_t)q0, (uint32_t)(q0 >> 32), (uint32_t)occ, (uint32_t)(occ >> 32));
+                E.wide_rec[2 * wpos + 1] = make_uint4((uint32_t)ng, (uint32_t)wc0, (uint32_t)idx, masks);
+            } else {  // one unit per colour; bits 8.. of the masks hold its lane + 1
+                uint64_t k = 0, ws = occ;
+                while (ws) {
+                    const uint32_t i = __ffsll((long long)ws) - 1;
+                    ws &= ws - 1;
+                    uint64_t x = E.stage[idx * E.WB + i];
+                    while (x) {
+                        const uint32_t c = __ffsll((long long)x) - 1;
+                        x &= x - 1;
+                        const uint64_t u = wpos + k;
+                        E.wide_rec[2 * u] = make_uint4((uint32_t)q0, (uint32_t)(q0 >> 32), i < 32 ? 1u << i : 0u,
+                                                       i < 32 ? 0u : 1u << (i - 32));
+                        E.wide_rec[2 * u + 1] = make_uint4((uint32_t)ng, (uint32_t)(wc0 + k * wck), (uint32_t)idx,
+                                                           masks | ((i * 64u + c + 1u) << 8));
+                        ++k;
+                    }
+                }
+            }
+        }
+        wgroups += wide ? wun * ng : 0;
         if (fits && !E.unfused) {
             write_unit(E, pos0, w, (uint32_t)idx, occ, 0u, rs, re, gbeg0, ng, false);
         } else if (fits) {
@@ -776,6 +972,26 @@ __device__ void dev_commit(const Eng& E, Smem& sm) {
             c0 = (uint32_t)((gbeg0 + kChunk - 1) / kChunk);
             nck = (uint32_t)((gbeg0 + ng + kChunk - 1) / kChunk) - c0;
         }
+        // wide chunk map first: chunk wc0 + r -> unit wpos + r / wck
+        {
+            const uint32_t wn = wfits ? (uint32_t)(wun * wck) : 0u;
+            const uint32_t wincl = warp_incl_scan(wn);
+            const uint32_t wtot = __shfl_sync(0xffffffffu, wincl, 31);
+            cw.start[lane] = wincl - wn;
+            cw.w[lane] = (uint32_t)wpos;
+            cw.occ_lo[lane] = (uint32_t)wc0;
+            cw.bits[lane] = (uint32_t)wck;
+            __syncwarp();
+            for (uint32_t t = lane; t < wtot; t += 32) {
+                uint32_t o = 0;
+#pragma unroll
+                for (uint32_t step = 16; step > 0; step >>= 1)
+                    if (cw.start[o + step] <= t) o += step;
+                const uint32_t r = t - cw.start[o];
+                E.wide_chunk[(uint64_t)cw.occ_lo[o] + r] = cw.w[o] + r / cw.bits[o];
+            }
+            __syncwarp();
+        }
         const uint32_t cincl = warp_incl_scan(nck);
         const uint32_t ctot = __shfl_sync(0xffffffffu, cincl, 31);
         cw.start[lane] = cincl - nck;
@@ -792,17 +1008,62 @@ __device__ void dev_commit(const Eng& E, Smem& sm) {
             else atomicOr(&ctl->error, (unsigned)kErrChunkOverflow);
         }
         __syncwarp();
+    };
+    if (!scan) {
+        for (uint64_t r0 = 0; r0 < P; r0 += nwarp * vpw) {
+            const uint64_t C = min((uint64_t)P - r0, nwarp * vpw);  // vertices of this round
+            const uint64_t nused = (C + vpw - 1) / vpw;
+            if (wid >= nused) break;  // only the last round leaves warps out
+            const uint64_t idx = r0 + wid + (uint64_t)lane * nused;
+            const bool ok = lane < vpw && idx < r0 + C;
+            uint32_t w = 0;
+            uint64_t m = 0, rs = 0, re = 0;
+            if (ok) {
+                w = L2(&E.pend_v[idx]);
+                m = L2(&E.nocc[w]);
+                E.nocc[w] = 0;
+                rs = __ldg(&E.rstart[w]);
+                re = __ldg(&E.rend[w]);
+            }
+            round(ok, w, idx, m, rs, re);
+        }
+    } else {
+        // the next warp-sized block's masks are loaded before this one is handled
+        uint64_t base = wid * 32;
+        uint64_t m = base + lane < E.n ? L2(&E.nocc[base + lane]) : 0ull;
+        for (; base < E.n; base += nwarp * 32) {
+            const uint64_t v = base + lane, nb = base + nwarp * 32;
+            const uint64_t mnext = nb + lane < E.n ? L2(&E.nocc[nb + lane]) : 0ull;
+            bool ok = m != 0;
+            if (__any_sync(0xffffffffu, ok)) {
+                if (ok) E.nocc[v] = 0;
+                uint64_t idx = warp_alloc<unsigned int>(&ctl->scan_rows, ok ? 1u : 0u);
+                if (ok && idx >= E.pend_cap) {
+                    atomicOr(&ctl->error, (unsigned)kErrPendOverflow);
+                    ok = false;
+                }
+                uint64_t rs = 0, re = 0;
+                if (ok) {
+                    rs = __ldg(&E.rstart[v]);
+                    re = __ldg(&E.rend[v]);
+                }
+                round(ok, (uint32_t)v, idx, ok ? m : 0ull, rs, re);
+            }
+            m = mnext;
+        }
     }
     mwords = warp_sum(mwords);
     ncol = warp_sum(ncol);
+    wgroups = warp_sum(wgroups);
     if (lane == 0 && mwords) atomicAdd(&ctl->st_mask_words, (unsigned long long)mwords);
     if (lane == 0 && ncol) atomicAdd(&ctl->new_colours, (unsigned long long)ncol);
+    if (lane == 0 && wgroups) atomicAdd(&ctl->wide_gnew, (unsigned long long)wgroups);
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < E.WB; i += blockDim.x) {
         const unsigned long long a = ((unsigned long long)sm.act[2 * i + 1] << 32) | sm.act[2 * i];
         if (a) atomicOr(&ctl->act_w[i], a);
     }
-    if (P) phase_end(ctl, 1);
+    if (P || scan) phase_end(ctl, 1);
 }
 
 // ---- level direction: degree-ratio heuristic and the policy network ----------------------
@@ -819,6 +1080,17 @@ __device__ __forceinline__ void level_features(float* f, double U, double G, dou
     f[5] = (float)log2(1.0 + C / (U > 1.0 ? U : 1.0));
 }
 
+// The policy's level actions: outputs 0..4 of the network are the predicted
+// log2 time of the level under each.
+constexpr uint32_t kActPush = 0, kActFiltered = 1, kActPull = 2, kActPushScan = 3, kActFilteredScan = 4;
+constexpr uint32_t kActions = 5;
+__device__ __forceinline__ uint32_t action_dir(uint32_t a) {
+    return a == kActPull ? kDirPull : (a == kActFiltered || a == kActFilteredScan) ? kDirFiltered : kDirPush;
+}
+__device__ __forceinline__ uint32_t action_mode(uint32_t a) {
+    return a >= kActPushScan ? FBPT_COMPACT_SCAN : FBPT_COMPACT_QUEUE;
+}
+
 // Push draws about G * (colours per unit) times; a pull level reads every
 // vertex's row and, at most, every edge.  Pull when the push would draw for more
 // colour-edges than twice the edge count; filter pushes whose units carry many
@@ -830,10 +1102,10 @@ __device__ __forceinline__ uint32_t heuristic_dir(double U, double G, double C, 
     return kDirPush;
 }
 
-// 6 -> 32 -> 32 -> 8 ReLU network; outputs 0..2 are the predicted log2 device
-// time of the level under push, filtered push and pull.  P holds the input
-// mean and scale (6 + 6), then W1 (32x6), b1, W2 (32x32), b2, W3 (8x32), b3.
-// All threads of the CTA call it.
+// 6 -> 32 -> 32 -> 8 ReLU network on the features in sm.rawf; outputs 0..2
+// are the predicted log2 device time of the level under push, filtered push
+// and pull.  P holds the input mean and scale (6 + 6), then W1 (32x6), b1,
+// W2 (32x32), b2, W3 (8x32), b3.  All threads of the CTA call it.
 __device__ void policy_forward(const float* P, Smem& sm) {
     const int t = threadIdx.x;
     const float* mu = P;
@@ -844,7 +1116,7 @@ __device__ void policy_forward(const float* P, Smem& sm) {
     const float* b2 = W2 + kPolicyHidden * kPolicyHidden;
     const float* W3 = b2 + kPolicyHidden;
     const float* b3 = W3 + kPolicyHidden * kPolicyOut;
-    if (t < kPolicyIn) sm.feat[t] = (sm.feat[t] - mu[t]) / sd[t];
+    if (t < kPolicyIn) sm.feat[t] = (sm.rawf[t] - mu[t]) / sd[t];
     __syncthreads();
     if (t < kPolicyHidden) {
         float h = b1[t];
@@ -940,6 +1212,12 @@ __device__ void dev_schedule(const Eng& E, Smem& sm) {
         case 15: h.tick_limit = L2(&ctl->tick_limit); break;
         case 16: case 17: case 18: h.ph_t0[t - 16] = L2(&ctl->ph_t0[t - 16]); break;
         case 19: case 20: case 21: h.ph_t1[t - 19] = L2(&ctl->ph_t1[t - 19]); break;
+        case 22: h.wide_packed = L2(&ctl->wide_packed); break;
+        case 23: h.wide_gnew = L2(&ctl->wide_gnew); break;
+        case 24: h.wide_units = L2(&ctl->wide_units); break;
+        case 25: h.wide_groups = L2(&ctl->wide_groups); break;
+        case 26: h.mode = L2(&ctl->mode); break;
+        case 27: h.scan_rows = L2(&ctl->scan_rows); break;
         default: break;
     }
     uint32_t per = 1;
@@ -1085,28 +1363,43 @@ __device__ void dev_schedule(const Eng& E, Smem& sm) {
     const bool any_run = nstill != 0 || assigned != 0;
     // 5. direction of the coming level
     {
-        const unsigned long long np = h.new_packed;
-        const double U = (double)(np & kUnitMask), G = (double)(np >> kUnitBits);
+        const unsigned long long np = h.new_packed, wp = h.wide_packed;
+        const double U = (double)((np & kUnitMask) + (wp & kUnitMask)), G = (double)((np >> kUnitBits) + h.wide_gnew);
         const double C = (double)h.new_colours;
         const uint32_t sched = h.sched;
         const bool pull_ok = E.frontd != nullptr;
         if (t == 0) {
-            if (sched == FBPT_SCHED_LEARNED && E.policy) level_features(sm.feat, U, G, C, (double)nstill, (double)E.m);
+            if ((sched == FBPT_SCHED_LEARNED && E.policy) || E.trace)
+                level_features(sm.rawf, U, G, C, (double)nstill, (double)E.m);
             uint32_t d = kDirPush;
             if (sched == FBPT_SCHED_PULL && pull_ok) d = kDirPull;
             else if (sched == FBPT_SCHED_FILTERED) d = kDirFiltered;
             else if (sched == FBPT_SCHED_HEURISTIC || sched == FBPT_SCHED_LEARNED)
                 d = heuristic_dir(U, G, C, (double)E.m, pull_ok);
+            // compaction: the option for fixed schedules; the heuristic scans when
+            // the level just done reached more than n / 16 vertices
+            const uint32_t reached = h.mode == FBPT_COMPACT_SCAN ? h.scan_rows : h.pend_count;
+            uint32_t md = E.compaction;
+            if (sched == FBPT_SCHED_HEURISTIC || sched == FBPT_SCHED_LEARNED)
+                md = (uint64_t)reached * 16 > (uint64_t)E.n ? FBPT_COMPACT_SCAN : FBPT_COMPACT_QUEUE;
+            if (d == kDirPull || E.model == FBPT_MODEL_LT) md = FBPT_COMPACT_QUEUE;
             sm.dir = d;
+            sm.mode = md;
         }
         __syncthreads();
         if (sched == FBPT_SCHED_LEARNED && E.policy) {
             policy_forward(E.policy, sm);
             if (t == 0) {
-                uint32_t best = kDirPush;
-                if (sm.out[kDirFiltered] < sm.out[best]) best = kDirFiltered;
-                if (pull_ok && sm.out[kDirPull] < sm.out[best]) best = kDirPull;
-                sm.dir = best;
+                // actions: push, filtered push, pull (queue compaction), then push
+                // and filtered push with scan compaction; the smallest predicted time
+                uint32_t best = kActPush;
+                for (uint32_t a = 1; a < kActions; ++a) {
+                    if (a == kActPull && !pull_ok) continue;
+                    if (a >= kActPushScan && E.model == FBPT_MODEL_LT) continue;
+                    if (sm.out[a] < sm.out[best]) best = a;
+                }
+                sm.dir = action_dir(best);
+                sm.mode = action_mode(best);
             }
             __syncthreads();
         }
@@ -1129,10 +1422,11 @@ __device__ void dev_schedule(const Eng& E, Smem& sm) {
         if (E.trace && tick < E.trace_cap) {
             fbpt_trace_row& row = E.trace[tick];
             row.level = tick;
-            row.units = h.list_count;
-            row.groups = h.list_groups;
+            row.units = h.list_count + h.wide_units;
+            row.groups = h.list_groups + h.wide_groups;
+            row.compaction = h.mode;
             row.colours = h.list_colours;
-            row.pending = h.pend_count;
+            row.pending = h.mode == FBPT_COMPACT_SCAN ? h.scan_rows : h.pend_count;
             row.active_lanes = nstill;
             row.finished_lanes = F;
             row.started_lanes = assigned;
@@ -1141,17 +1435,34 @@ __device__ void dev_schedule(const Eng& E, Smem& sm) {
             row.direction = h.dir;
             row.frontier_lanes = h.frontier_lanes;
         }
+        // the features and network outputs the coming level's decision used
+        if (E.trace && tick + 1 < E.trace_cap) {
+            fbpt_trace_row& nx = E.trace[tick + 1];
+            const bool net = h.sched == FBPT_SCHED_LEARNED && E.policy;
+            for (int k = 0; k < kPolicyIn; ++k) nx.features[k] = sm.rawf[k];
+            for (int k = 0; k < kPolicyOut; ++k) nx.outputs[k] = net ? sm.out[k] : 0.f;
+        }
         ctl->list_colours = err ? 0 : h.new_colours;
         ctl->new_colours = 0;
         ctl->next_j = h.next_j + assigned;
         atomicAdd(&ctl->st_assigned, assigned);
-        const unsigned long long np = h.new_packed;
+        const unsigned long long np = h.new_packed, wp = h.wide_packed;
         ctl->list_count = err ? 0 : (np & kUnitMask);
         ctl->list_groups = err ? 0 : (np >> kUnitBits);
-        atomicAdd(&ctl->st_units, np & kUnitMask);
-        if (h.list_groups != 0) atomicAdd(h.dir == kDirPull ? &ctl->st_pull : &ctl->st_push, 1ull);
-        if (h.dir != kDirPull) atomicAdd(&ctl->st_groups, h.list_groups);
+        ctl->wide_units = err ? 0 : (wp & kUnitMask);
+        ctl->wide_chunks = err ? 0 : (wp >> kUnitBits);
+        ctl->wide_groups = err ? 0 : h.wide_gnew;
+        ctl->wide_packed = 0;
+        ctl->wide_gnew = 0;
+        ctl->wchunk_next = 0;
+        for (uint32_t k = 0; k < kWideQueues; ++k) ctl->wqueue[k * 32] = 0;
+        atomicAdd(&ctl->st_units, (np & kUnitMask) + (wp & kUnitMask));
+        const unsigned long long lg = h.list_groups + h.wide_groups;
+        if (lg != 0) atomicAdd(h.dir == kDirPull ? &ctl->st_pull : &ctl->st_push, 1ull);
+        if (h.dir != kDirPull) atomicAdd(&ctl->st_groups, lg);
         ctl->dir = sm.dir;
+        ctl->mode = sm.mode;
+        ctl->scan_rows = 0;
         ctl->frontier_lanes = nstill;
         for (int p = 0; p < 3; ++p) {
             if (h.ph_t1[p] > h.ph_t0[p]) atomicAdd(&ctl->st_phase_ns[p], h.ph_t1[p] - h.ph_t0[p]);
@@ -1184,11 +1495,13 @@ __global__ void __launch_bounds__(kThreads) k_sweep(const Eng E) {
 }
 __global__ void __launch_bounds__(kThreads, FBPT_EXPAND_MINB) k_expand(const Eng E) {
     __shared__ uint32_t lane_j[kMaxLanes];
-    dev_expand<kPartPush>(E, lane_j);
+    __shared__ uint32_t pcnt[kThreads / 32], pbuf[kThreads / 32 * kPendBuf];
+    dev_expand<kPartPush>(E, lane_j, pcnt, pbuf);
 }
 __global__ void __launch_bounds__(kThreads) k_expand_alt(const Eng E) {
     __shared__ uint32_t lane_j[kMaxLanes];
-    dev_expand<kPartAlt>(E, lane_j);
+    __shared__ uint32_t pcnt[kThreads / 32], pbuf[kThreads / 32 * kPendBuf];
+    dev_expand<kPartAlt>(E, lane_j, pcnt, pbuf);
 }
 __global__ void __launch_bounds__(kThreads) k_commit(const Eng E) {
     __shared__ Smem sm;
@@ -1252,7 +1565,7 @@ __global__ void __launch_bounds__(kThreads) k_run(const Eng E) {
     for (;;) {
         dev_sweep(E, sm.lane, sm.fin);  // lanes finished at the previous level
         dev_init(E);       // lanes given a sample at the previous level
-        dev_expand<kPartAll>(E, sm.lane);
+        dev_expand<kPartAll>(E, sm.lane, sm.pcnt, sm.pbuf);
         if (!grid_barrier(E, sm, gen, false)) return;
         dev_commit(E, sm);
         if (!grid_barrier(E, sm, gen, true)) return;
@@ -1432,7 +1745,8 @@ int order_rows(const uint32_t* rows_v, const uint64_t* row_start, const uint32_t
 // list, col/thr and the lanes' sample ids and writes next[], nocc[] and the
 // pending list, so the two may overlap; the commit waits for both.
 int launch_level(const Eng& E, cudaStream_t st, int blocks, cudaStream_t side = nullptr,
-                 cudaEvent_t fork = nullptr, cudaEvent_t join = nullptr) {
+                 cudaEvent_t fork = nullptr, cudaEvent_t join = nullptr, cudaEvent_t ex0 = nullptr,
+                 cudaEvent_t ex1 = nullptr) {
     if (side) {
         FBPT_CUDA_TRY(cudaEventRecord(fork, st));
         FBPT_CUDA_TRY(cudaStreamWaitEvent(side, fork, 0));
@@ -1441,8 +1755,10 @@ int launch_level(const Eng& E, cudaStream_t st, int blocks, cudaStream_t side = 
     } else {
         k_sweep<<<blocks, kThreads, 0, st>>>(E);
     }
+    if (ex0) FBPT_CUDA_TRY(cudaEventRecord(ex0, st));
     k_expand<<<blocks, kThreads, 0, st>>>(E);
     if (E.alt) k_expand_alt<<<blocks, kThreads, 0, st>>>(E);
+    if (ex1) FBPT_CUDA_TRY(cudaEventRecord(ex1, st));
     if (side) FBPT_CUDA_TRY(cudaStreamWaitEvent(st, join, 0));
     k_commit<<<blocks, kThreads, 0, st>>>(E);
     k_schedule<<<1, kSchedThreads, 0, st>>>(E);
@@ -1551,6 +1867,7 @@ void ws_free(Workspace* w) {
     cudaFree(w->visited); cudaFree(w->next); cudaFree(w->nocc); cudaFree(w->stage); cudaFree(w->pend_v);
     cudaFree(w->seg); cudaFree(w->spill); cudaFree(w->list_v); cudaFree(w->list_mrow); cudaFree(w->list_only); cudaFree(w->list_rs);
     cudaFree(w->list_re); cudaFree(w->list_g); cudaFree(w->list_occ); cudaFree(w->chunk_u0); cudaFree(w->ctl);
+    cudaFree(w->wide_rec); cudaFree(w->wide_chunk);
     cudaFree(w->frontd); cudaFree(w->fstamp);
     if (w->ctl_host) cudaFreeHost(w->ctl_host);
     delete w;
@@ -1589,6 +1906,8 @@ int ws_get(fbpt_graph* g, uint32_t WB, bool unfused, bool dense, cudaStream_t st
     // groups of a row [rs, re) are at most (re - rs) / 4 + 2
     const uint64_t max_groups = (g->m / 4 + 2 * n + 1) * (unfused ? 64ull * WB : 1ull);
     w->chunk_cap = std::min<uint64_t>(max_groups / kChunk + 2, 0xFFFFFFFFull);
+    // a wide unit's chunks are at most twice its groups / 32 (it has >= 32 groups)
+    w->wide_chunk_cap = std::min<uint64_t>(2 * (max_groups / kChunk) + 2, 0xFFFFFFFFull);
     w->spill_cap = std::max<uint64_t>(1ull << 22, 4 * n);
     int rc = FBPT_OK;
     size_t& b = w->bytes;
@@ -1608,6 +1927,8 @@ int ws_get(fbpt_graph* g, uint32_t WB, bool unfused, bool dense, cudaStream_t st
     if (rc == FBPT_OK) rc = dalloc(&w->list_g, w->list_cap, b);
     if (rc == FBPT_OK) rc = dalloc(&w->list_occ, w->list_cap, b);
     if (rc == FBPT_OK) rc = dalloc(&w->chunk_u0, w->chunk_cap, b);
+    if (rc == FBPT_OK) rc = dalloc(&w->wide_rec, 2 * w->list_cap, b);
+    if (rc == FBPT_OK) rc = dalloc(&w->wide_chunk, w->wide_chunk_cap, b);
     if (rc == FBPT_OK) rc = dalloc(&w->ctl, 1, b);
     if (rc == FBPT_OK && dense) rc = dalloc(&w->frontd, rows, b);
     if (rc == FBPT_OK && dense) rc = dalloc(&w->fstamp, n, b);
@@ -1647,6 +1968,7 @@ struct Run {
     uint32_t* row_len = nullptr;    // S
     fbpt_trace_row* dtrace = nullptr;
     uint32_t* order = nullptr;      // S: sample index of each refill position (sorted starts), or NULL
+    double expand_event_ms = 0.0;   // host-launched levels: CUDA-event time of the expand launches
     Ctl* H = nullptr;               // pinned: the initial control block in, the final one out
     Eng E = {};
 };
@@ -1727,6 +2049,8 @@ int run_setup(Run& r, fbpt_graph* g, uint64_t seed, uint64_t first_id, uint64_t 
         return fail(FBPT_EINVAL, "fbpt_sample: bad launch mode");
     if (o.refill != FBPT_REFILL_LANE && o.refill != FBPT_REFILL_BATCH)
         return fail(FBPT_EINVAL, "fbpt_sample: bad refill mode");
+    if (o.compaction != FBPT_COMPACT_QUEUE && o.compaction != FBPT_COMPACT_SCAN)
+        return fail(FBPT_EINVAL, "fbpt_sample: bad compaction mode");
     r.g = g;
     r.seed = seed;
     r.first_id = first_id;
@@ -1788,11 +2112,13 @@ int run_arm(Run& r) {
     if (r.rows_v) cudaFreeAsync(r.rows_v, r.st);
     r.rows_v = nullptr;
     FBPT_CUDA_TRY(cudaMallocAsync(&r.rows_v, sizeof(uint32_t) * r.cap, r.st));
+    if (r.dtrace) FBPT_CUDA_TRY(cudaMemsetAsync(r.dtrace, 0, sizeof(fbpt_trace_row) * r.o.trace_cap, r.st));
     Ctl* H = r.H;
     std::memset(H, 0, sizeof(Ctl));
     H->S = r.S;
     H->sched = r.o.schedule;
     H->dir = r.o.schedule == FBPT_SCHED_FILTERED ? kDirFiltered : kDirPush;
+    H->mode = FBPT_COMPACT_QUEUE;  // the first levels carry only the start vertices
     H->refill = r.o.refill == FBPT_REFILL_BATCH ? kRefillBatch : kRefillLane;
     H->pair_cap = r.cap;
     for (int p = 0; p < 3; ++p) H->ph_t0[p] = ~0ull;
@@ -1809,16 +2135,26 @@ int run_arm(Run& r) {
     E.inv = g->inv;
     E.order = r.order;
     E.seed = r.seed; E.first_id = r.first_id; E.S = r.S;
+    {
+        uint32_t a = (uint32_t)r.seed, b = (uint32_t)(r.seed >> 32);
+        for (int k = 0; k < 10; ++k, a += kPhiloxW0, b += kPhiloxW1) {
+            E.key0[k] = a;
+            E.key1[k] = b;
+        }
+    }
     E.visited = ws->visited; E.next = ws->next; E.nocc = ws->nocc; E.stage = ws->stage;
     E.pend_v = ws->pend_v; E.seg = ws->seg; E.seg_cap = ws->seg_cap; E.spill = ws->spill;
     E.list_v = ws->list_v; E.list_mrow = ws->list_mrow; E.list_only = ws->list_only;
     E.list_rs = ws->list_rs; E.list_re = ws->list_re; E.list_g = ws->list_g; E.list_occ = ws->list_occ;
     E.chunk_u0 = ws->chunk_u0;
+    E.wide_rec = ws->wide_rec; E.wide_chunk = ws->wide_chunk; E.wide_chunk_cap = ws->wide_chunk_cap;
     E.orow = g->orow; E.odst = g->odst; E.oeid = g->oeid;
     E.frontd = ws->frontd; E.fstamp = ws->fstamp;
     E.policy = (r.o.schedule == FBPT_SCHED_LEARNED && r.o.policy) ? r.o.policy->d_params : nullptr;
     E.alt = r.o.schedule == FBPT_SCHED_PUSH ? 0u : 1u;
     E.model = r.o.model;
+    E.compaction = r.o.compaction == FBPT_COMPACT_SCAN && r.o.schedule != FBPT_SCHED_PULL ? FBPT_COMPACT_SCAN
+                                                                                       : FBPT_COMPACT_QUEUE;
     E.wpre = g->wpre;
     E.m = g->m;
     E.pend_cap = ws->pend_cap; E.list_cap = ws->list_cap; E.chunk_cap = ws->chunk_cap;
@@ -1849,15 +2185,30 @@ int run_enqueue(Run& r) {
     } else if (r.o.launch == FBPT_LAUNCH_PERSISTENT) {
         rc = run_persistent(r.E, st);
     } else {
+        // host-driven levels: the expand launches are bracketed by CUDA events
+        // (the level waits for the host anyway), summed into ms_expand_events
+        cudaEvent_t ex0 = nullptr, ex1 = nullptr;
+        if (cudaEventCreate(&ex0) != cudaSuccess || cudaEventCreate(&ex1) != cudaSuccess) {
+            if (ex0) cudaEventDestroy(ex0);
+            cudaGetLastError();
+            return fail(FBPT_ECUDA, "level loop: event create failed");
+        }
+        r.expand_event_ms = 0.0;
         for (;;) {
-            rc = launch_level(r.E, st, r.blocks);
+            rc = launch_level(r.E, st, r.blocks, nullptr, nullptr, nullptr, ex0, ex1);
             if (rc != FBPT_OK) break;
             if (cudaMemcpyAsync(&r.H->running, &ws->ctl->running, sizeof(unsigned), cudaMemcpyDeviceToHost, st) !=
                     cudaSuccess ||
-                cudaStreamSynchronize(st) != cudaSuccess)
-                return fail(FBPT_ECUDA, std::string("level loop: ") + cudaGetErrorString(cudaGetLastError()));
+                cudaStreamSynchronize(st) != cudaSuccess) {
+                rc = fail(FBPT_ECUDA, std::string("level loop: ") + cudaGetErrorString(cudaGetLastError()));
+                break;
+            }
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, ex0, ex1) == cudaSuccess) r.expand_event_ms += ms;
             if (!r.H->running) break;
         }
+        cudaEventDestroy(ex0);
+        cudaEventDestroy(ex1);
         if (rc == FBPT_OK) rc = launch_final_sweep(r.E, st, r.blocks);
     }
     if (rc != FBPT_OK) return rc;
@@ -1960,6 +2311,7 @@ int run_finish(Run& r, fbpt_stats* stats) {
         stats->ms_expand += 1e-6 * (double)H->st_phase_ns[0];
         stats->ms_commit += 1e-6 * (double)H->st_phase_ns[1];
         stats->ms_sweep += 1e-6 * (double)H->st_phase_ns[2];
+        stats->ms_expand_events += r.expand_event_ms;
     }
     return FBPT_OK;
 }
@@ -2162,6 +2514,50 @@ int sample_batched_impl(uint32_t G, fbpt_graph* const* gs, const uint64_t* seeds
     const float ms = elapsed_ms(ev.a, ev.b);
     if (stats) stats->ms_total += ms;
     cudaFreeHost(Hs);
+    return FBPT_OK;
+}
+
+// The policy network's row-width choice: one probe at the reference shape
+// (8 words x 1 slot, lane refill, the learned schedule) records the network's
+// outputs 5..7 on every level (predicted log2 ns per sample at row widths of
+// 4, 16 and 64 words); their means over the probe's levels rank the widths.
+int policy_width_impl(fbpt_graph* g, uint64_t seed, uint64_t S, const fbpt_opts* base, uint32_t* row_words,
+                      float* scores) {
+    if (!g || !base || !row_words) return fail(FBPT_EINVAL, "fbpt_policy_width: null argument");
+    if (!base->policy) return fail(FBPT_EINVAL, "fbpt_policy_width: needs a policy");
+    if (S == 0) return fail(FBPT_EINVAL, "fbpt_policy_width: S must be >= 1");
+    fbpt_opts q = *base;
+    q.schedule = FBPT_SCHED_LEARNED;
+    q.words = 8;
+    q.slots = 1;
+    q.refill = FBPT_REFILL_LANE;
+    q.unfused = 0;
+    q.blocks = 0;
+    if (q.launch == FBPT_LAUNCH_PERSISTENT) q.launch = FBPT_LAUNCH_GRAPH;
+    const uint64_t P = std::min<uint64_t>(S, 8192);
+    std::vector<fbpt_trace_row> rows(1u << 16);
+    q.trace = rows.data();
+    q.trace_cap = rows.size();
+    fbpt_rrsets rr;
+    fbpt_stats st = {};
+    FBPT_TRY(sample_impl(g, seed, 0, P, &q, &rr, &st));
+    release_out(&rr);
+    double sum[kPolicyWidthCount] = {};
+    uint64_t cnt = 0;
+    for (uint64_t r = 1; r < st.trace_rows; ++r) {
+        if (rows[r].units == 0) continue;
+        for (uint32_t k = 0; k < kPolicyWidthCount; ++k) sum[k] += rows[r].outputs[kPolicyWidthOut + k];
+        ++cnt;
+    }
+    uint32_t best = kPolicyWidthCount - 1;  // no level with a frontier: the widest row
+    if (cnt) {
+        best = 0;
+        for (uint32_t k = 1; k < kPolicyWidthCount; ++k)
+            if (sum[k] < sum[best]) best = k;
+    }
+    *row_words = kPolicyWidths[best];
+    if (scores)
+        for (uint32_t k = 0; k < kPolicyWidthCount; ++k) scores[k] = cnt ? (float)(sum[k] / (double)cnt) : 0.f;
     return FBPT_OK;
 }
 

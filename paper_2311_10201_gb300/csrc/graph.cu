@@ -133,6 +133,7 @@ extern "C" int fbpt_graph_create(uint32_t n, uint64_t m, const uint64_t* row_ptr
     if (mem_kind != FBPT_MEM_HOST && mem_kind != FBPT_MEM_DEVICE)
         return fail(FBPT_EINVAL, "fbpt_graph_create: bad mem_kind");
     cudaStream_t st = (cudaStream_t)stream;
+    FBPT_TRY(noalloc_preload());
     fbpt_graph* g = new fbpt_graph();
     g->n = n;
     g->m = m;

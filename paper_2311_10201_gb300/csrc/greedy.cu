@@ -6,7 +6,6 @@
 // (vertex -> rows containing it) turns each pick into a walk over the newly
 // covered rows, decrementing the gain of every vertex in them.
 #include <algorithm>
-#include <mutex>
 #include <string>
 
 #include "internal.cuh"
@@ -154,6 +153,10 @@ extern "C" int fbpt_select_seeds(const fbpt_rrsets* rr, uint32_t k, uint32_t* se
 // fbpt_select_seeds_noalloc gives them the same greedy picks as
 // fbpt_select_seeds with its working memory in the file-scope array below:
 // every GPU that loads libfbpt holds these 64 MiB until the process exits.
+// CUDA places a module's device arrays when the module is loaded on a device,
+// and by default it loads modules lazily, on first use; so graph creation
+// (noalloc_preload) touches the array, which loads this file's module while
+// the caller can still allocate, and the later call needs nothing new.
 // Instead of an inverted index it finds, each round, the uncovered rows that
 // contain the pick by a binary search in every row (rows are ascending).
 
@@ -162,10 +165,6 @@ namespace {
 
 constexpr size_t kNoAllocScratchBytes = 64ull << 20;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
-
-constexpr int kMaxDevices = 64;
-std::mutex g_noalloc_mu;
-void* g_noalloc_base[kMaxDevices] = {};
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -196,26 +195,27 @@ __global__ void k_cover_rows(const unsigned long long* best, uint32_t r, uint32_
     }
 }
 
-// Device address of the scratch array on the current device, looked up once
-// per device.
+// Device address of the scratch array on the current device, looked up on
+// every call (a host-side cache could outlive the context that it came from,
+// e.g. across a cudaDeviceReset; the lookup costs next to nothing).
 int noalloc_base(void** out) {
-    int dev = 0;
-    FBPT_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kMaxDevices) return fail(FBPT_EUNSUPPORTED, "fbpt_select_seeds_noalloc: device index");
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_base[dev]) {
-        void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p)
-            return fail(FBPT_ECUDA, std::string("fbpt_select_seeds_noalloc: cudaGetSymbolAddress: ") +
-                                        cudaGetErrorString(e));
-        g_noalloc_base[dev] = p;
-    }
-    *out = g_noalloc_base[dev];
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+        return fail(FBPT_ECUDA, std::string("fbpt_select_seeds_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    *out = p;
     return FBPT_OK;
 }
 
 }  // namespace
+
+// Loads this file's module (and so places the scratch array) on the current
+// device; called when a graph is created there.
+int noalloc_preload() {
+    void* p = nullptr;
+    return noalloc_base(&p);
+}
+
 }  // namespace fbpt
 
 extern "C" int fbpt_select_seeds_noalloc(const fbpt_rrsets* rr, uint32_t k, uint32_t* seeds_host,

@@ -18,10 +18,23 @@ constexpr uint64_t kSegBytesMax = 2ull << 30;  // largest segment array of a wor
 constexpr uint32_t kSpillPosBits = 26;
 constexpr uint64_t kSpillMask = (1ull << kSpillPosBits) - 1;
 constexpr uint32_t kChunk = 32;         // 4-edge groups per expand chunk (one per lane)
+// Frontier units with at least this many 4-edge groups are "wide": each of
+// their expand chunks is 32 groups of that unit alone (the lanes share its
+// colours); narrower units are packed 32 groups per chunk across units.
+constexpr uint32_t kWideMin = 32;
+constexpr uint32_t kPendBuf = 32;       // per-warp buffer of new pending vertices in the expand
 #ifndef FBPT_CHUNKS_PER_GRAB
 #define FBPT_CHUNKS_PER_GRAB 2
 #endif
 constexpr uint32_t kChunksPerGrab = FBPT_CHUNKS_PER_GRAB;  // chunks a warp takes per atomic
+#ifndef FBPT_WIDE_QUEUES
+#define FBPT_WIDE_QUEUES 8
+#endif
+// The wide chunks of a level are split into this many contiguous ranges, each
+// with its own counter (on its own 128-byte line), so that the warps' grabs
+// do not all meet on one address; a warp starts on the range of its index and
+// moves on when a range runs out.
+constexpr uint32_t kWideQueues = FBPT_WIDE_QUEUES;
 
 enum ErrorBits : uint32_t {
     kErrListOverflow = 1u,
@@ -40,6 +53,9 @@ enum Direction : uint32_t {
 };
 constexpr uint32_t kPullMaxWords = 8;  // pull levels need WB <= 8 (dense frontier rows)
 constexpr int kPolicyIn = 6, kPolicyHidden = 32, kPolicyOut = 8;
+// outputs 5..7 of the policy network rank these row widths (words)
+constexpr uint32_t kPolicyWidthOut = 5, kPolicyWidthCount = 3;
+constexpr uint32_t kPolicyWidths[kPolicyWidthCount] = {4, 16, 64};
 constexpr int kPolicyParams = kPolicyIn * kPolicyHidden + kPolicyHidden + kPolicyHidden * kPolicyHidden +
                               kPolicyHidden + kPolicyHidden * kPolicyOut + kPolicyOut;
 
@@ -86,6 +102,15 @@ struct Ctl {
     unsigned long long st_edges, st_calls, st_units, st_cev, st_assigned, st_push, st_pull, st_mask_words;
     unsigned long long st_groups;
     unsigned long long new_colours, list_colours;  // colour bits of the new / current frontier units
+    // wide units: the commit's allocation counter (units | chunks << 26) and
+    // their groups; the coming expand's units, chunks and groups; its chunk counter
+    unsigned long long wide_packed, wide_gnew;
+    unsigned long long wide_units, wide_chunks, wide_groups;
+    unsigned int wchunk_next, wpad;
+    unsigned int wqueue[kWideQueues * 32];  // wide-chunk counters, one per 128-byte line
+    // compaction of the coming level (fbpt_compaction); stage rows the scan
+    // commit has handed out
+    unsigned int mode, scan_rows;
     // phase times: first CTA start .. last CTA end of each phase (%globaltimer, ns);
     // index 0 expand, 1 commit, 2 sweep
     unsigned long long ph_t0[3], ph_t1[3], st_phase_ns[3];
@@ -113,6 +138,9 @@ struct Workspace {
     uint64_t* list_g = nullptr;
     uint64_t* list_occ = nullptr;
     uint32_t* chunk_u0 = nullptr; // chunk_cap
+    uint4* wide_rec = nullptr;    // 2 * list_cap: wide unit records (32 B each)
+    uint32_t* wide_chunk = nullptr; // wide_chunk_cap: unit of each wide chunk
+    uint64_t wide_chunk_cap = 0;
     uint64_t* frontd = nullptr;   // n * WB when pull levels are allowed: frontier rows by vertex
     uint32_t* fstamp = nullptr;   // n: level whose frontier frontd[v] holds
     uint64_t pend_cap = 0, list_cap = 0, chunk_cap = 0, spill_cap = 0;
@@ -124,6 +152,7 @@ struct Workspace {
 
 // Kernel parameters of one run (passed by value).
 struct Eng {
+    uint32_t key0[10], key1[10];  // Philox round keys of seed (k0 + r * W0, k1 + r * W1), set by the host
     uint32_t n, WB;
     const uint64_t* row_ptr;
     const uint32_t* col;
@@ -145,6 +174,12 @@ struct Eng {
     uint64_t* list_g;
     uint64_t* list_occ;
     uint32_t* chunk_u0;
+    // wide unit u: wide_rec[2u] = (first group lo, hi, colour words lo, hi),
+    // wide_rec[2u + 1] = (groups, first chunk, stage row, edge masks: bits 0-3
+    // the in-row edges of the first group, 4-7 those of the last)
+    uint4* wide_rec;
+    uint32_t* wide_chunk;
+    uint64_t wide_chunk_cap;
     const uint64_t* orow;         // out-edge CSR (pull)
     const uint32_t* odst;
     const uint32_t* oeid;
@@ -153,6 +188,7 @@ struct Eng {
     const float* policy;          // kPolicyParams weights of the schedule network, or NULL
     const uint64_t* wpre;         // LT: exclusive prefix of the edge weights (m + 1)
     uint32_t model;               // fbpt_model
+    uint32_t compaction;          // fbpt_compaction of fixed schedules
     uint64_t m;
     uint64_t pend_cap, list_cap, chunk_cap, spill_cap;
     uint32_t unfused;
@@ -223,6 +259,8 @@ int sample_impl(fbpt_graph* g, uint64_t seed, uint64_t first_id, uint64_t S, con
 int sample_batched_impl(uint32_t G, fbpt_graph* const* gs, const uint64_t* seeds, const uint64_t* first_ids,
                         const uint64_t* Ss, const fbpt_opts* opts, fbpt_rrsets* outs, fbpt_stats* stats);
 int autotune_impl(fbpt_graph* g, uint64_t seed, uint64_t S, const fbpt_opts* base, fbpt_tuning* out);
+int policy_width_impl(fbpt_graph* g, uint64_t seed, uint64_t S, const fbpt_opts* base, uint32_t* row_words,
+                      float* scores);
 int imm_impl(fbpt_graph* g, uint32_t k, double epsilon, double ell, uint64_t seed, uint64_t max_samples,
              const fbpt_opts* opts, uint32_t* seeds_host, uint64_t* gains_host, fbpt_imm_result* result,
              fbpt_stats* stats);
@@ -239,4 +277,7 @@ int radix_sort_u64(uint64_t* keys, uint64_t* tmp, uint64_t n, uint32_t bits, cud
 // start vertex, ties by index (g->sorted_starts); caller frees with cudaFreeAsync.
 int start_order(const fbpt_graph* g, uint64_t seed, uint64_t first_id, uint64_t S, cudaStream_t st,
                 uint32_t** order);
+// Places fbpt_select_seeds_noalloc's fixed scratch array on the current device
+// (its module is loaded on first use; graph creation calls this).
+int noalloc_preload();
 }  // namespace fbpt

@@ -167,6 +167,9 @@ __global__ void __launch_bounds__(256) k_mlp_grad(const float* __restrict__ P, c
         if (g[i] != 0.f) atomicAdd(&grad[i], g[i]);
 }
 
+// One Adam step (Kingma and Ba, ICLR 2015, Algorithm 1: beta1 = 0.9, beta2 =
+// 0.999, eps = 1e-8) on the weights and biases; the input mean and scale
+// (the first 12 floats) are not trained.
 __global__ void k_adam(float* P, const float* grad, float* m, float* v, int t, float lr) {
     const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
     const float c1 = 1.f - powf(b1, (float)t), c2 = 1.f - powf(b2, (float)t);
@@ -180,37 +183,46 @@ __global__ void k_adam(float* P, const float* grad, float* m, float* v, int t, f
     }
 }
 
+// Device buffers of one training call, allocated and freed on its stream.
 struct TrainBufs {
+    cudaStream_t st = nullptr;
     float *P = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr, *loss = nullptr, *X = nullptr, *Y = nullptr;
     uint32_t* A = nullptr;
+    explicit TrainBufs(cudaStream_t s) : st(s) {}
     ~TrainBufs() {
-        cudaFree(P); cudaFree(grad); cudaFree(m); cudaFree(v); cudaFree(loss); cudaFree(X); cudaFree(Y); cudaFree(A);
+        for (void* p : {(void*)P, (void*)grad, (void*)m, (void*)v, (void*)loss, (void*)X, (void*)Y, (void*)A})
+            if (p) cudaFreeAsync(p, st);
+        cudaStreamSynchronize(st);
     }
 };
 
+// Parameters (and, with rows > 0, the trace rows) to the device; Adam moments zeroed.
 int upload(TrainBufs& b, const float* params, const float* X, const uint32_t* A, const float* Y, uint64_t rows) {
-    FBPT_CUDA_TRY(cudaMalloc(&b.P, sizeof(float) * kNP));
-    FBPT_CUDA_TRY(cudaMalloc(&b.grad, sizeof(float) * kNP));
-    FBPT_CUDA_TRY(cudaMalloc(&b.m, sizeof(float) * kNP));
-    FBPT_CUDA_TRY(cudaMalloc(&b.v, sizeof(float) * kNP));
-    FBPT_CUDA_TRY(cudaMalloc(&b.loss, sizeof(float)));
-    FBPT_CUDA_TRY(cudaMalloc(&b.X, sizeof(float) * kPolicyIn * rows));
-    FBPT_CUDA_TRY(cudaMalloc(&b.Y, sizeof(float) * rows));
-    FBPT_CUDA_TRY(cudaMalloc(&b.A, sizeof(uint32_t) * rows));
-    FBPT_CUDA_TRY(cudaMemcpy(b.P, params, sizeof(float) * kNP, cudaMemcpyHostToDevice));
-    FBPT_CUDA_TRY(cudaMemcpy(b.X, X, sizeof(float) * kPolicyIn * rows, cudaMemcpyHostToDevice));
-    FBPT_CUDA_TRY(cudaMemcpy(b.Y, Y, sizeof(float) * rows, cudaMemcpyHostToDevice));
-    FBPT_CUDA_TRY(cudaMemcpy(b.A, A, sizeof(uint32_t) * rows, cudaMemcpyHostToDevice));
-    FBPT_CUDA_TRY(cudaMemset(b.m, 0, sizeof(float) * kNP));
-    FBPT_CUDA_TRY(cudaMemset(b.v, 0, sizeof(float) * kNP));
+    const cudaStream_t st = b.st;
+    FBPT_CUDA_TRY(cudaMallocAsync((void**)&b.P, sizeof(float) * kNP, st));
+    FBPT_CUDA_TRY(cudaMallocAsync((void**)&b.grad, sizeof(float) * kNP, st));
+    FBPT_CUDA_TRY(cudaMallocAsync((void**)&b.m, sizeof(float) * kNP, st));
+    FBPT_CUDA_TRY(cudaMallocAsync((void**)&b.v, sizeof(float) * kNP, st));
+    FBPT_CUDA_TRY(cudaMallocAsync((void**)&b.loss, sizeof(float), st));
+    FBPT_CUDA_TRY(cudaMemcpyAsync(b.P, params, sizeof(float) * kNP, cudaMemcpyHostToDevice, st));
+    FBPT_CUDA_TRY(cudaMemsetAsync(b.m, 0, sizeof(float) * kNP, st));
+    FBPT_CUDA_TRY(cudaMemsetAsync(b.v, 0, sizeof(float) * kNP, st));
+    if (rows) {
+        FBPT_CUDA_TRY(cudaMallocAsync((void**)&b.X, sizeof(float) * kPolicyIn * rows, st));
+        FBPT_CUDA_TRY(cudaMallocAsync((void**)&b.Y, sizeof(float) * rows, st));
+        FBPT_CUDA_TRY(cudaMallocAsync((void**)&b.A, sizeof(uint32_t) * rows, st));
+        FBPT_CUDA_TRY(cudaMemcpyAsync(b.X, X, sizeof(float) * kPolicyIn * rows, cudaMemcpyHostToDevice, st));
+        FBPT_CUDA_TRY(cudaMemcpyAsync(b.Y, Y, sizeof(float) * rows, cudaMemcpyHostToDevice, st));
+        FBPT_CUDA_TRY(cudaMemcpyAsync(b.A, A, sizeof(uint32_t) * rows, cudaMemcpyHostToDevice, st));
+    }
     return FBPT_OK;
 }
 
 int grad_pass(TrainBufs& b, uint64_t rows) {
-    FBPT_CUDA_TRY(cudaMemset(b.grad, 0, sizeof(float) * kNP));
-    FBPT_CUDA_TRY(cudaMemset(b.loss, 0, sizeof(float)));
+    FBPT_CUDA_TRY(cudaMemsetAsync(b.grad, 0, sizeof(float) * kNP, b.st));
+    FBPT_CUDA_TRY(cudaMemsetAsync(b.loss, 0, sizeof(float), b.st));
     const int blocks = (int)std::min<uint64_t>((rows + 255) / 256, (uint64_t)device_sm_count() * 2);
-    k_mlp_grad<<<std::max(blocks, 1), 256>>>(b.P, b.X, b.A, b.Y, rows, b.grad, b.loss);
+    k_mlp_grad<<<std::max(blocks, 1), 256, 0, b.st>>>(b.P, b.X, b.A, b.Y, rows, b.grad, b.loss);
     FBPT_CUDA_TRY(cudaGetLastError());
     return FBPT_OK;
 }
@@ -233,15 +245,34 @@ double normal01(uint64_t& s) {
 }  // namespace fbpt
 
 extern "C" int fbpt_policy_loss_grad(const float* params, const float* features, const uint32_t* actions,
-                                     const float* targets, uint64_t rows, float* loss, float* grad) {
+                                     const float* targets, uint64_t rows, float* loss, float* grad, void* stream) {
     if (!params || !features || !actions || !targets || rows == 0 || !loss || !grad)
         return fail(FBPT_EINVAL, "fbpt_policy_loss_grad: bad arguments");
-    TrainBufs b;
+    TrainBufs b((cudaStream_t)stream);
     FBPT_TRY(upload(b, params, features, actions, targets, rows));
     FBPT_TRY(grad_pass(b, rows));
-    FBPT_CUDA_TRY(cudaMemcpy(grad, b.grad, sizeof(float) * kNP, cudaMemcpyDeviceToHost));
-    FBPT_CUDA_TRY(cudaMemcpy(loss, b.loss, sizeof(float), cudaMemcpyDeviceToHost));
+    FBPT_CUDA_TRY(cudaMemcpyAsync(grad, b.grad, sizeof(float) * kNP, cudaMemcpyDeviceToHost, b.st));
+    FBPT_CUDA_TRY(cudaMemcpyAsync(loss, b.loss, sizeof(float), cudaMemcpyDeviceToHost, b.st));
+    FBPT_CUDA_TRY(cudaStreamSynchronize(b.st));
     for (int i = 0; i < kOffW1; ++i) grad[i] = 0.f;
+    return FBPT_OK;
+}
+
+extern "C" int fbpt_policy_adam_step(float* params, const float* grad, float* m, float* v, uint32_t t, float lr,
+                                     void* stream) {
+    if (!params || !grad || !m || !v || t == 0 || !(lr > 0.f))
+        return fail(FBPT_EINVAL, "fbpt_policy_adam_step: bad arguments");
+    TrainBufs b((cudaStream_t)stream);
+    FBPT_TRY(upload(b, params, nullptr, nullptr, nullptr, 0));
+    FBPT_CUDA_TRY(cudaMemcpyAsync(b.grad, grad, sizeof(float) * kNP, cudaMemcpyHostToDevice, b.st));
+    FBPT_CUDA_TRY(cudaMemcpyAsync(b.m, m, sizeof(float) * kNP, cudaMemcpyHostToDevice, b.st));
+    FBPT_CUDA_TRY(cudaMemcpyAsync(b.v, v, sizeof(float) * kNP, cudaMemcpyHostToDevice, b.st));
+    k_adam<<<8, 256, 0, b.st>>>(b.P, b.grad, b.m, b.v, (int)t, lr);
+    FBPT_CUDA_TRY(cudaGetLastError());
+    FBPT_CUDA_TRY(cudaMemcpyAsync(params, b.P, sizeof(float) * kNP, cudaMemcpyDeviceToHost, b.st));
+    FBPT_CUDA_TRY(cudaMemcpyAsync(m, b.m, sizeof(float) * kNP, cudaMemcpyDeviceToHost, b.st));
+    FBPT_CUDA_TRY(cudaMemcpyAsync(v, b.v, sizeof(float) * kNP, cudaMemcpyDeviceToHost, b.st));
+    FBPT_CUDA_TRY(cudaStreamSynchronize(b.st));
     return FBPT_OK;
 }
 
@@ -281,14 +312,17 @@ extern "C" int fbpt_policy_train(const float* features, const uint32_t* actions,
         for (uint64_t r = 0; r < rows; ++r) ym += targets[r];
         for (int i = 0; i < kPolicyOut; ++i) P[kOffB3 + i] = (float)(ym / rows);
     }
-    TrainBufs b;
+    TrainBufs b((cudaStream_t)o.stream);
     FBPT_TRY(upload(b, P, features, actions, targets, rows));
     for (uint32_t t = 1; t <= steps; ++t) {
         FBPT_TRY(grad_pass(b, rows));
-        k_adam<<<8, 256>>>(b.P, b.grad, b.m, b.v, (int)t, lr);
+        k_adam<<<8, 256, 0, b.st>>>(b.P, b.grad, b.m, b.v, (int)t, lr);
     }
     FBPT_TRY(grad_pass(b, rows));
-    FBPT_CUDA_TRY(cudaMemcpy(P, b.P, sizeof(P), cudaMemcpyDeviceToHost));
-    if (final_loss) FBPT_CUDA_TRY(cudaMemcpy(final_loss, b.loss, sizeof(float), cudaMemcpyDeviceToHost));
+    FBPT_CUDA_TRY(cudaMemcpyAsync(P, b.P, sizeof(P), cudaMemcpyDeviceToHost, b.st));
+    float fl = 0.f;
+    FBPT_CUDA_TRY(cudaMemcpyAsync(&fl, b.loss, sizeof(float), cudaMemcpyDeviceToHost, b.st));
+    FBPT_CUDA_TRY(cudaStreamSynchronize(b.st));
+    if (final_loss) *final_loss = fl;
     return fbpt_policy_create(P, kNP, out);
 }

@@ -246,3 +246,48 @@ def test_long_rr_sets_grow_the_spill_log(fbpt):
     assert np.diff(ref.offsets).max() > 1024
     assert rr.stats.overflow_reruns >= 1
     assert_same(rr, ref, g)
+
+
+# ---- frontier compaction: pending queue vs scan of the occupancy masks -----------------------
+
+@pytest.mark.parametrize("launch", ["host", "graph", "persistent"])
+@pytest.mark.parametrize("schedule", ["push", "filtered"])
+@pytest.mark.parametrize("which", ["rmat12", "rmat12_dense", "rmat13_wc"])
+def test_scan_compaction_gives_the_same_bits(fbpt, request, which, schedule, launch):
+    """Levels whose reached vertices are found by scanning every vertex's
+    word-occupancy mask (no pending list, no returned atomics in the expand)
+    give the same RR sets as the queue."""
+    g = request.getfixturevalue(which)
+    dg = fbpt.Graph.from_synth(g)
+    ref = oracle.rr_sets(g, SEED, 3, 1200)
+    for words, slots, refill in ((4, 2, "lane"), (1, 1, "batch"), (8, 8, "lane")):
+        rr = fbpt.sample(dg, SEED, 3, 1200, words=words, slots=slots, refill=refill, schedule=schedule,
+                         launch=launch, compaction="scan", trace_cap=1 << 14 if launch == "host" else 0)
+        assert_same(rr, ref, g)
+        if rr.trace is not None:
+            tr = rr.trace[1:]
+            assert np.all(tr["compaction"][tr["units"] > 0] == 1)
+
+
+def test_heuristic_switches_compaction_on_dense_levels(fbpt, rmat12_dense):
+    """The heuristic scans when a level reached more than n / 16 vertices:
+    on a supercritical graph both modes occur in one run, with the same bits."""
+    dg = fbpt.Graph.from_synth(rmat12_dense)
+    rr = fbpt.sample(dg, SEED, 0, 2048, words=4, slots=2, schedule="heuristic", launch="graph", trace_cap=8192)
+    modes = set(np.unique(rr.trace["compaction"]).tolist())
+    assert modes == {0, 1}
+    assert_same(rr, oracle.rr_sets(rmat12_dense, SEED, 0, 2048), rmat12_dense)
+
+
+@pytest.mark.parametrize("launch", ["graph", "persistent"])
+def test_unfused_wide_units_bit_exact(fbpt, rmat13_wc, launch):
+    """Unfused runs on a weighted-cascade graph whose hubs have at least 32
+    4-edge groups: each (vertex, colour) unit of a hub gets chunks of its own."""
+    g = rmat13_wc
+    assert int(np.max(np.diff(g.row_ptr.astype(np.int64)))) >= 4 * 32
+    dg = fbpt.Graph.from_synth(g)
+    ref = oracle.rr_sets(g, SEED, 0, 1500)
+    for compaction in ("queue", "scan"):
+        rr = fbpt.sample(dg, SEED, 0, 1500, words=2, slots=1, refill="batch", unfused=True, launch=launch,
+                         compaction=compaction)
+        assert_same(rr, ref, g)

@@ -2,6 +2,8 @@
 device memory is all in their own pool, or who must stay clear of the
 allocator) gives the same seeds and gains as fbpt_select_seeds, through the C
 ABI, on two calls in a row over different RR sets.  Collected last."""
+import os
+
 import numpy as np
 import pytest
 
@@ -39,3 +41,41 @@ def test_noalloc_rejects_sizes_beyond_its_array():
         fbpt.select_seeds_noalloc(rr, 3)
     assert ei.value.code == fbpt.EINVAL
     assert "67108864" in str(ei.value)
+
+
+_NEARLY_FULL = r"""
+import sys
+sys.path.insert(0, sys.argv[1])
+import numpy as np, torch, synth
+import paper_2311_10201_gb300 as fbpt
+g = synth.rmat_wc(12, seed=31)
+dg = fbpt.Graph.from_synth(g)
+rr = fbpt.sample(dg, synth.SAMPLE_SEED, 0, 4000)
+torch.cuda.synchronize()
+free, _ = torch.cuda.mem_get_info()
+pool = torch.empty(max(free - (48 << 20), 0), dtype=torch.uint8, device="cuda")
+got = fbpt.select_seeds_noalloc(rr, 30)
+del pool
+torch.cuda.empty_cache()
+want = fbpt.select_seeds(rr, 30)
+assert np.array_equal(got[0], want[0]) and np.array_equal(got[1], want[1]), (got, want)
+print("ok")
+"""
+
+
+def test_noalloc_selection_with_device_memory_nearly_full():
+    """A caller that created its graph and RR sets, then gave almost all free
+    device memory to its own pool (here a torch tensor), still gets the same
+    seeds.  Run in a fresh process, where nothing but graph creation has
+    touched the seed-selection code before the memory is taken: the fixed
+    array was placed then, and the call needs no memory beyond it."""
+    import subprocess
+    import sys
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    import paper_2311_10201_gb300 as fbpt
+    fbpt.build()
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", _NEARLY_FULL, root], capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0 and r.stdout.strip().endswith("ok"), r.stdout[-2000:] + r.stderr[-2000:]
