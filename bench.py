@@ -141,44 +141,73 @@ def run_reference(args):
 
 def bench_batched(fbpt, torch, stream, steps, schedule):
     """The 32-graph workload (R-MAT scales 12-20, edge factors 8-32, uniform p
-    in [0.01, 0.1], 4,096-262,144 samples per graph): the learned schedule with
-    per-graph autotuned shapes in one batched CUDA-graph launch, against the
-    plain fused form run graph after graph.  Each arm has its own graph
-    handles (and so its own workspaces); each is warmed up once."""
+    in [0.01, 0.1], 4,096-262,144 samples per graph), from the plain fused form
+    to the learned batched form one change at a time (each arm warmed up once,
+    then `steps` timed calls; all arms give the same bits):
+      plain            graph after graph, one host launch per level, 8-word
+                       batches run to completion, push levels
+      lane_refill      the same with lane refill
+      tuned            each graph at its autotuned row width and CTA count, its
+                       levels in one CUDA-graph launch, push levels
+      batched_push     the tuned shapes, every graph in ONE CUDA-graph launch
+      batched_heuristic / batched_learned   the same shapes under the degree-
+                       ratio heuristic / the policy network's schedule
+      learned_batched  the autotuner's pick of shape and schedule (it judges
+                       the learned schedule against the heuristic and push)."""
     w = synth.batched_32()
     total = sum(w.S)
     firsts = [0] * len(w.graphs)
+    dgs = [fbpt.Graph.from_synth(g, stream) for g in w.graphs]
+    t0 = time.perf_counter()
+    tuned = [fbpt.autotune(dg, seed, S, schedule=schedule) for dg, seed, S in zip(dgs, w.seeds, w.S)]
+    tune_s = time.perf_counter() - t0
     arms = {}
-    for arm in ("learned_batched", "plain"):
-        dgs = [fbpt.Graph.from_synth(g, stream) for g in w.graphs]
-        t0 = time.perf_counter()
-        if arm == "learned_batched":
-            for dg, seed, S in zip(dgs, w.seeds, w.S):
-                fbpt.autotune(dg, seed, S, schedule=schedule)
-            kw = dict(schedule=schedule)
-        else:
-            kw = dict(launch="host", words=8, slots=1, refill="batch", schedule="push")
-        tune_s = time.perf_counter() - t0
-        outs, _ = fbpt.sample_batched(dgs, w.seeds, firsts, w.S, stream=stream, **kw)
-        del outs
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(steps):
+
+    def run_arm(name, call):
+        ms, st = timed_calls(torch, stream, call, steps)
+        arms[name] = {"value": total / (ms / 1e3), "unit": "RR samples/s", "ms_per_step": ms,
+                      "colour_edge_visits_per_s": st.colour_edge_visits / (ms / 1e3), "levels": int(st.levels),
+                      "rr_entries": int(st.rr_total)}
+
+    def batched(**kw):
+        def call():
             outs, st = fbpt.sample_batched(dgs, w.seeds, firsts, w.S, stream=stream, **kw)
-            rr_total = sum(rr.total for rr in outs)
             del outs
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / steps
-        arms[arm] = {"value": total / (ms / 1e3), "unit": "RR samples/s", "ms_per_step": ms,
-                     "colour_edge_visits_per_s": st.colour_edge_visits / (ms / 1e3), "rr_entries": rr_total,
-                     "levels": st.levels, "tune_s": tune_s if arm == "learned_batched" else None}
-        for dg in dgs:
-            dg.close()
-    return {"graphs": len(w.graphs), "samples": total, "steps": steps, **arms,
-            "speedup": arms["learned_batched"]["value"] / arms["plain"]["value"]}
+            return st
+        return call
+
+    def one_by_one(kws):
+        def call():
+            agg = fbpt.Stats()
+            for dg, seed, S, kw in zip(dgs, w.seeds, w.S, kws):
+                rr = fbpt.sample(dg, seed, 0, S, stream=stream, **kw)
+                for k in ("levels", "colour_edge_visits", "rr_total"):
+                    setattr(agg, k, getattr(agg, k) + getattr(rr.stats, k))
+                del rr
+            return agg
+        return call
+
+    run_arm("plain", batched(launch="host", words=8, slots=1, refill="batch", schedule="push"))
+    run_arm("lane_refill", batched(launch="host", words=8, slots=1, refill="lane", schedule="push"))
+    shapes = [dict(words=t["words"], slots=t["slots"], blocks=t["blocks"], refill="lane") for t in tuned]
+    run_arm("tuned", one_by_one([dict(s, schedule="push", launch="graph") for s in shapes]))
+    for sched in ("push", "heuristic", "learned"):
+        for dg, sh in zip(dgs, shapes):
+            fbpt.set_tuning(dg, sh["words"], sh["slots"], "lane", sh["blocks"], sched)
+        run_arm("batched_" + sched, batched(schedule=sched))
+    for dg, t in zip(dgs, tuned):
+        fbpt.set_tuning(dg, t["words"], t["slots"], "lane", t["blocks"], t["schedule"])
+    run_arm("learned_batched", batched(schedule=schedule))
+    for dg in dgs:
+        dg.close()
+    base = arms["plain"]["value"]
+    out = {"graphs": len(w.graphs), "samples": total, "steps": steps, "tune_s": tune_s,
+           "tuned_schedules": {k: sum(1 for t in tuned if t["schedule"] == k) for k in ("push", "heuristic", "learned")},
+           **arms}
+    out["speedup"] = arms["learned_batched"]["value"] / base
+    out["steps_over_plain"] = {k: v["value"] / base for k, v in arms.items()}
+    out["learned_over_heuristic"] = arms["batched_learned"]["value"] / arms["batched_heuristic"]["value"]
+    return out
 
 
 def timed_calls(torch, stream, call, steps):
@@ -227,6 +256,47 @@ def bench_fused_unfused(fbpt, torch, stream, steps):
     return out
 
 
+def bench_s24(fbpt, torch, stream, samples, chunk, words=8):
+    """R-MAT scale 24 with trivalency p per edge (16,777,216 vertices, ~263M
+    in-edges), sample ids 0 .. samples-1 in calls of `chunk` samples (each
+    call's RR sets are built in full, then released: the whole output would
+    not fit in memory), at 8-word rows with lane refill, under the policy
+    network's schedule and under the degree-ratio heuristic.  Greedy k = 200
+    runs on the first chunk's sets."""
+    w = synth.rmat_s24_tri()
+    g, seed = w.graphs[0], w.seeds[0]
+    t0 = time.perf_counter()
+    dg = fbpt.Graph.from_synth(g, stream)
+    upload_s = time.perf_counter() - t0
+    out = {"workload": "rmat_s24_tri", "n": g.n, "m": g.m, "samples": samples, "chunk": chunk, "words": words,
+           "upload_s": upload_s}
+    for sched in ("learned", "heuristic"):
+        kw = dict(words=words, slots=1, refill="lane", schedule=sched, launch="graph")
+        warm = fbpt.sample(dg, seed, 0, min(chunk, 1024), stream=stream, **kw)
+        del warm
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        agg = {"levels": 0, "pull_levels": 0, "colour_edge_visits": 0, "rr_total": 0, "philox_calls": 0}
+        e0.record(stream)
+        for c0 in range(0, samples, chunk):
+            rr = fbpt.sample(dg, seed, c0, min(chunk, samples - c0), stream=stream, **kw)
+            if c0 == 0 and sched == "learned":
+                seeds, _ = fbpt.select_seeds(rr, w.k)
+            st = rr.stats
+            for k in agg:
+                agg[k] += int(getattr(st, k))
+            del rr
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out[sched] = {"value": samples / (ms / 1e3), "unit": "RR samples/s", "ms": ms,
+                      "colour_edge_visits_per_s": agg["colour_edge_visits"] / (ms / 1e3), **agg}
+    out["learned_over_heuristic"] = out["learned"]["value"] / out["heuristic"]["value"]
+    dg.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -248,6 +318,13 @@ def main():
     ap.add_argument("--order", default="identity", choices=["identity", "rcm", "degree", "random", "cluster"],
                     help="vertex order of the sampled graph (host preprocessing, outside the timed steps)")
     ap.add_argument("--sorted-starts", action="store_true", help="samples take lanes by start vertex")
+    ap.add_argument("--fused-steps", type=int, default=2,
+                    help="timed calls per arm of the fused-vs-unfused W sweep on R-MAT s20 (0 = skip)")
+    ap.add_argument("--s24-samples", type=int, default=65536,
+                    help="samples of the R-MAT s24 trivalency measurement (0 = skip; 4194304 = the full workload)")
+    ap.add_argument("--s24-chunk", type=int, default=8192, help="samples per sampling call on R-MAT s24")
+    ap.add_argument("--only", default=None, choices=["batched", "fused", "s24"],
+                    help="run one comparison alone and print its object")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -263,6 +340,16 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     fbpt.build()
+    if args.only:
+        stream = torch.cuda.current_stream()
+        if args.only == "batched":
+            res = bench_batched(fbpt, torch, stream, max(args.batched_steps, 1), args.schedule)
+        elif args.only == "fused":
+            res = bench_fused_unfused(fbpt, torch, stream, max(args.fused_steps, 1))
+        else:
+            res = bench_s24(fbpt, torch, stream, args.s24_samples, args.s24_chunk)
+        print(json.dumps({"only": args.only, args.only: res}))
+        return
     w, g = build_workload(args.workload)
     S = args.samples
     k = w.k or 100
@@ -428,6 +515,15 @@ def main():
     batched = None
     if rank == 0 and world == 1 and args.batched_steps > 0:
         batched = bench_batched(fbpt, torch, stream, args.batched_steps, args.schedule)
+    fused = None
+    if rank == 0 and world == 1 and args.fused_steps > 0:
+        fused = bench_fused_unfused(fbpt, torch, stream, args.fused_steps)
+    s24 = None
+    if rank == 0 and world == 1 and args.s24_samples > 0:
+        try:
+            s24 = bench_s24(fbpt, torch, stream, args.s24_samples, args.s24_chunk)
+        except Exception as ex:  # reported, never fatal to the line
+            s24 = {"error": str(ex)[:200]}
 
     # ---- roofline of the dominant kernel (the push expand), per launch ----
     # HBM is the roofline: nothing on the path is a dense contraction.
@@ -515,6 +611,7 @@ def main():
                        "shape": kw, "autotuned": tuned, "order": args.order, "sorted_starts": args.sorted_starts,
                        "l2": "inputs larger than L2 (in-CSR + thresholds %.0f MB)" % ((g.m * 8 + g.n * 8) / 1e6)},
             "plain_fused": plain, "ordered": ordered, "lt": lt, "batched_32": batched, "imm": imm,
+            "fused_vs_unfused_s20": fused, "s24_tri": s24,
             "colour_edge_visits_per_s": st.colour_edge_visits * world / (ms_step / 1e3),
             "stats": st.as_dict(),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,

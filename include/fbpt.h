@@ -330,6 +330,11 @@ int fbpt_policy_width(fbpt_graph* g, uint64_t seed, uint64_t S, const fbpt_opts*
 
 /* The shape stored on g by fbpt_autotune; FBPT_EINVAL if it was never tuned. */
 int fbpt_graph_tuning(const fbpt_graph* g, fbpt_tuning* out);
+/* Stores a shape on g as fbpt_autotune would (words in {1, 2, 4, 8}, slots >= 1,
+ * words * slots <= 64, a valid refill mode and schedule; blocks 0 = every CTA
+ * the GPU holds), e.g. to run the batched form at one shape under several
+ * schedules.  FBPT_EINVAL otherwise. */
+int fbpt_graph_set_tuning(fbpt_graph* g, const fbpt_tuning* t);
 
 int fbpt_rrsets_free(fbpt_rrsets* rr);
 /* Host copies (any pointer may be NULL): offsets[S+1], verts[total], starts[S], vcount[n]. */

@@ -110,6 +110,7 @@ _SIGS = {
     "fbpt_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.POINTER(Opts),
                                      ctypes.POINTER(Tuning)]),
     "fbpt_graph_tuning": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Tuning)]),
+    "fbpt_graph_set_tuning": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Tuning)]),
     "fbpt_policy_width": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.POINTER(Opts),
                                          U32P, ctypes.POINTER(ctypes.c_float)]),
     "fbpt_imm": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
@@ -395,6 +396,16 @@ def policy_width(g: Graph, seed: int, S: int, policy=None, stream=None, launch="
     scores = (ctypes.c_float * 3)()
     _check(lib().fbpt_policy_width(g._h, seed, S, ctypes.byref(o), ctypes.byref(words), scores))
     return int(words.value), [float(x) for x in scores]
+
+
+def set_tuning(g: Graph, words, slots, refill="lane", blocks=0, schedule="push"):
+    """Store a launch shape on g (fbpt_graph_set_tuning), used by the batched
+    call when words == 0."""
+    t = Tuning()
+    t.words, t.slots, t.blocks = int(words), int(slots), int(blocks)
+    t.refill = REFILL[refill] if isinstance(refill, str) else int(refill)
+    t.schedule = SCHED[schedule] if isinstance(schedule, str) else int(schedule)
+    _check(lib().fbpt_graph_set_tuning(g._h, ctypes.byref(t)))
 
 
 def tuning(g: Graph) -> dict:

@@ -117,6 +117,18 @@ extern "C" int fbpt_policy_width(fbpt_graph* g, uint64_t seed, uint64_t S, const
     }
 }
 
+extern "C" int fbpt_graph_set_tuning(fbpt_graph* g, const fbpt_tuning* t) {
+    if (!g || !t) return fail(FBPT_EINVAL, "fbpt_graph_set_tuning: null argument");
+    if (t->words != 1 && t->words != 2 && t->words != 4 && t->words != 8)
+        return fail(FBPT_EINVAL, "fbpt_graph_set_tuning: words must be 1, 2, 4 or 8");
+    if (t->slots < 1 || t->words * t->slots > 64) return fail(FBPT_EINVAL, "fbpt_graph_set_tuning: words * slots > 64");
+    if (t->refill > FBPT_REFILL_BATCH || t->schedule > FBPT_SCHED_FILTERED)
+        return fail(FBPT_EINVAL, "fbpt_graph_set_tuning: bad refill or schedule");
+    g->tuned = *t;
+    g->tuned_valid = true;
+    return FBPT_OK;
+}
+
 extern "C" int fbpt_graph_tuning(const fbpt_graph* g, fbpt_tuning* out) {
     if (!g || !out) return fail(FBPT_EINVAL, "fbpt_graph_tuning: null argument");
     if (!g->tuned_valid) return fail(FBPT_EINVAL, "fbpt_graph_tuning: graph was never tuned");

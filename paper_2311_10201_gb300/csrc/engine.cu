@@ -51,9 +51,7 @@ constexpr int kThreads = 256;
 #ifndef FBPT_EXPAND_MINB
 #define FBPT_EXPAND_MINB 3  // resident CTAs per SM the expand kernel is compiled for
 #endif
-#ifndef FBPT_EXPAND_PREFETCH
-#define FBPT_EXPAND_PREFETCH 1  // wide expand: prefetch the next chunk's threshold vectors
-#endif
+
 
 __device__ __forceinline__ uint64_t row_groups(uint64_t rs, uint64_t re) {
     return re > rs ? ((re - 1) >> 2) - (rs >> 2) + 1 : 0;
@@ -391,6 +389,15 @@ __device__ __forceinline__ void group_draws(const Eng& E, const uint32_t* lj, ui
     }
 }
 
+// The set bits of x after dropping its lowest `skip` set bits, at most `take`
+// of them (the lowest).
+__device__ __forceinline__ uint64_t colour_slice(uint64_t x, uint32_t skip, uint32_t take) {
+    for (uint32_t k = 0; k < skip; ++k) x &= x - 1;
+    uint64_t rest = x;
+    for (uint32_t k = 0; k < take && rest; ++k) rest &= rest - 1;
+    return x & ~rest;
+}
+
 // Visited words (word i) of the four sources of group q, for filtered push;
 // ~0 for edges outside the row, so that they never veto a draw.
 __device__ __forceinline__ void source_visited(const Eng& E, uint64_t q, uint32_t vm, uint32_t i, uint64_t (&vis)[4]) {
@@ -401,9 +408,63 @@ __device__ __forceinline__ void source_visited(const Eng& E, uint64_t q, uint32_
     vis[3] = (vm & 8u) ? L2(&E.visited[(uint64_t)c4.w * E.WB + i]) : ~0ull;
 }
 
-// Wide units: a chunk is 32 consecutive groups of ONE unit, so the unit
-// record, its colour words and each draw's colour are warp-uniform; lane l
-// takes group 32 * (chunk - first chunk of the unit) + l.
+// The draws of two groups (q and q + 32: one lane's pair in a wide chunk) for
+// the colours x of word i: two independent Philox chains per colour, sharing
+// the colour's sample id; live colours gathered per half-word and edge.
+__device__ __forceinline__ void pair_draws(const Eng& E, const uint32_t* lj, uint64_t x, uint32_t i, uint64_t q,
+                                           const uint4& Ta, uint32_t sa, const uint4& Tb, uint32_t sb,
+                                           const PhiloxKeys& K, bool scan, uint32_t* cnt, uint32_t* buf) {
+    const uint32_t f_lo = (uint32_t)E.first_id, f_hi = (uint32_t)(E.first_id >> 32);
+    const uint64_t qb = q + kChunk;
+    const uint32_t qalo = (uint32_t)q, qahi = (uint32_t)(q >> 32), qblo = (uint32_t)qb, qbhi = (uint32_t)(qb >> 32);
+#pragma unroll 1
+    for (int h = 0; h < 2; ++h) {
+        uint32_t xx = (uint32_t)(x >> (32 * h));
+        uint32_t a0 = 0, a1 = 0, a2 = 0, a3 = 0, b0 = 0, b1 = 0, b2 = 0, b3 = 0;
+        const uint32_t* l = lj + 32 * h;
+        while (xx) {
+            const uint32_t c = __ffs(xx) - 1;
+            xx &= xx - 1;
+            const uint32_t j = l[c];
+            const uint32_t slo = f_lo + j;
+            const uint32_t shi = f_hi + (slo < j ? 1u : 0u);
+            const uint4 r = philox4x32_10(make_uint4(slo, shi, qalo, qahi), K);
+            const uint4 t = philox4x32_10(make_uint4(slo, shi, qblo, qbhi), K);
+            const uint32_t bit = 1u << c;
+            if ((r.x < Ta.x) | (r.y < Ta.y) | (r.z < Ta.z) | (r.w < Ta.w) | (sa != 0u)) {
+                if ((r.x < Ta.x) || (sa & 1u)) a0 |= bit;
+                if ((r.y < Ta.y) || (sa & 2u)) a1 |= bit;
+                if ((r.z < Ta.z) || (sa & 4u)) a2 |= bit;
+                if ((r.w < Ta.w) || (sa & 8u)) a3 |= bit;
+            }
+            if ((t.x < Tb.x) | (t.y < Tb.y) | (t.z < Tb.z) | (t.w < Tb.w) | (sb != 0u)) {
+                if ((t.x < Tb.x) || (sb & 1u)) b0 |= bit;
+                if ((t.y < Tb.y) || (sb & 2u)) b1 |= bit;
+                if ((t.z < Tb.z) || (sb & 4u)) b2 |= bit;
+                if ((t.w < Tb.w) || (sb & 8u)) b3 |= bit;
+            }
+        }
+        if (a0 | a1 | a2 | a3) {
+            const uint4 c4 = __ldg(reinterpret_cast<const uint4*>(E.col) + q);
+            if (a0) push_live(E, c4.x, i, (uint64_t)a0 << (32 * h), scan, cnt, buf);
+            if (a1) push_live(E, c4.y, i, (uint64_t)a1 << (32 * h), scan, cnt, buf);
+            if (a2) push_live(E, c4.z, i, (uint64_t)a2 << (32 * h), scan, cnt, buf);
+            if (a3) push_live(E, c4.w, i, (uint64_t)a3 << (32 * h), scan, cnt, buf);
+        }
+        if (b0 | b1 | b2 | b3) {
+            const uint4 c4 = __ldg(reinterpret_cast<const uint4*>(E.col) + qb);
+            if (b0) push_live(E, c4.x, i, (uint64_t)b0 << (32 * h), scan, cnt, buf);
+            if (b1) push_live(E, c4.y, i, (uint64_t)b1 << (32 * h), scan, cnt, buf);
+            if (b2) push_live(E, c4.z, i, (uint64_t)b2 << (32 * h), scan, cnt, buf);
+            if (b3) push_live(E, c4.w, i, (uint64_t)b3 << (32 * h), scan, cnt, buf);
+        }
+    }
+}
+
+// Wide units: a chunk is kWideSpan consecutive groups of ONE unit (lane l
+// takes groups l and l + 32 of it), times a block of at most kColourBlock of
+// the unit's colours, so the unit record, its colour words and each draw's
+// colour are warp-uniform.
 template <bool filtered, bool ro>
 __device__ __forceinline__ void expand_wide(const Eng& E, const uint32_t* lane_j, const PhiloxKeys& K, uint64_t NC,
                                             bool scan, uint32_t* cnt, uint32_t* buf, uint64_t& n_edges,
@@ -411,56 +472,75 @@ __device__ __forceinline__ void expand_wide(const Eng& E, const uint32_t* lane_j
     Ctl* ctl = E.ctl;
     const uint32_t lane = lane_id();
     const uint4* thr4 = reinterpret_cast<const uint4*>(E.thr);
-    const uint32_t wq0 = (uint32_t)(((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) % kWideQueues;
-    for (uint32_t qi = 0; qi < kWideQueues; ++qi) {
-      const uint32_t qn = (wq0 + qi) % kWideQueues;
-      const uint32_t qb = (uint32_t)(NC * qn / kWideQueues), qe = (uint32_t)(NC * (qn + 1) / kWideQueues);
-      for (;;) {
+    for (;;) {
         uint32_t c0 = 0;
-        if (lane == 0) c0 = qb + atomicAdd(&ctl->wqueue[qn * 32], kChunksPerGrab);
+        if (lane == 0) c0 = atomicAdd(&ctl->wchunk_next, kChunksPerGrab);
         c0 = __shfl_sync(0xffffffffu, c0, 0);
-        if (c0 >= qe) break;
-        const uint32_t c1 = min(c0 + kChunksPerGrab, qe);
+        if (c0 >= NC) break;
+        const uint32_t c1 = (uint32_t)min((uint64_t)c0 + kChunksPerGrab, NC);
         for (uint32_t c = c0; c < c1; ++c) {
             const uint32_t u = LD<ro>(&E.wide_chunk[c]);
             const uint4 ra = LD<ro>(&E.wide_rec[2ull * u]);
             const uint4 rb = LD<ro>(&E.wide_rec[2ull * u + 1]);
-            const uint32_t gl = kChunk * (c - rb.y) + lane;
+            // chunk r of the unit: group block gb, colour block cb
+            const uint32_t r = c - rb.y, ngb = (rb.x + kWideSpan - 1) / kWideSpan;
+            uint32_t gb = r, cb = 0;
+            if (r >= ngb) {
+                cb = r / ngb;
+                gb = r - cb * ngb;
+            }
+            const uint32_t gl = kWideSpan * gb + lane;
             const uint64_t q = (((uint64_t)ra.y << 32) | ra.x) + gl;
-            uint32_t vm = gl < rb.x ? 0xFu : 0u;
-            if (gl == 0) vm &= rb.w & 0xFu;
-            if (gl + 1 == rb.x) vm &= (rb.w >> 4) & 0xFu;
-            uint4 t = make_uint4(0u, 0u, 0u, 0u);
-            if (vm) t = __ldg(thr4 + q);
-#if FBPT_EXPAND_PREFETCH
-            // the next chunk of a grab is mostly the next 32 groups of the same
-            // unit: its threshold vectors head for L2 while this chunk draws
-            if (c + 1 < c1) asm volatile("prefetch.global.L2 [%0];" ::"l"(thr4 + q + kChunk));
-#endif
-            uint4 T;
-            const uint32_t sure = group_thresholds(vm, t, T);
-            n_edges += __popc(vm);
-            const bool need = draw_edges(T, sure) != 0u;
-            if (__any_sync(0xffffffffu, (T.x | T.y | T.z | T.w) != 0u)) {
+            // in-row edges of the lane's two groups
+            uint32_t vma = gl < rb.x ? 0xFu : 0u, vmb = gl + kChunk < rb.x ? 0xFu : 0u;
+            if (gl == 0) vma &= rb.w & 0xFu;
+            if (gl + 1 == rb.x) vma &= (rb.w >> 4) & 0xFu;
+            if (gl + kChunk + 1 == rb.x) vmb &= (rb.w >> 4) & 0xFu;
+            uint4 ta = make_uint4(0u, 0u, 0u, 0u), tb = ta;
+            if (vma) ta = __ldg(thr4 + q);
+            if (vmb) tb = __ldg(thr4 + q + kChunk);
+            uint4 Ta, Tb;
+            const uint32_t sa = group_thresholds(vma, ta, Ta), sb = group_thresholds(vmb, tb, Tb);
+            if (cb == 0) n_edges += __popc(vma) + __popc(vmb);
+            const uint32_t need = (draw_edges(Ta, sa) != 0u ? 1u : 0u) + (draw_edges(Tb, sb) != 0u ? 1u : 0u);
+            const bool any_a = (Ta.x | Ta.y | Ta.z | Ta.w) != 0u, any_b = (Tb.x | Tb.y | Tb.z | Tb.w) != 0u;
+            if (__any_sync(0xffffffffu, any_a || any_b)) {
                 uint64_t words = ((uint64_t)ra.w << 32) | ra.z;
-                while (words) {
+                // the unit's colours in (word, bit) order: skip cb blocks, take one
+                uint32_t skip = cb * kColourBlock, take = kColourBlock;
+                while (words && take) {
                     const uint32_t i = __ffsll((long long)words) - 1;
                     words &= words - 1;
                     const uint32_t only = rb.w >> 8;  // unfused: the unit's single colour (lane + 1)
                     uint64_t x = only ? 1ull << ((only - 1u) & 63u) : LD<ro>(&E.stage[(uint64_t)rb.z * E.WB + i]);
-                    uint64_t vis[4] = {0ull, 0ull, 0ull, 0ull};
-                    if (filtered) {
-                        if (vm) source_visited(E, q, vm, i, vis);
-                        x &= ~(vis[0] & vis[1] & vis[2] & vis[3]);
+                    const uint32_t pc = __popcll(x);
+                    if (skip >= pc) {
+                        skip -= pc;
+                        continue;
                     }
-                    if (need) n_calls += __popcll(x);
-                    group_draws<filtered>(E, lane_j + (i << 6), (T.x | T.y | T.z | T.w) ? x : 0ull, i, q, T, sure, K,
-                                          vis, scan, cnt, buf);
+                    if (skip || pc - skip > take) x = colour_slice(x, skip, take);
+                    skip = 0;
+                    take -= __popcll(x);
+                    n_calls += (uint64_t)need * __popcll(x);
+                    if (!filtered) {
+                        pair_draws(E, lane_j + (i << 6), (any_a || any_b) ? x : 0ull, i, q, Ta, sa, Tb, sb, K, scan,
+                                   cnt, buf);
+                    } else {
+#pragma unroll 1
+                        for (int g2 = 0; g2 < 2; ++g2) {
+                            const uint32_t vm = g2 ? vmb : vma;
+                            const uint64_t qq = g2 ? q + kChunk : q;
+                            uint64_t vis[4] = {~0ull, ~0ull, ~0ull, ~0ull};
+                            if (vm) source_visited(E, qq, vm, i, vis);
+                            const uint64_t xs = (g2 ? any_b : any_a) ? x & ~(vis[0] & vis[1] & vis[2] & vis[3]) : 0ull;
+                            group_draws<true>(E, lane_j + (i << 6), xs, i, qq, g2 ? Tb : Ta, g2 ? sb : sa, K, vis,
+                                              scan, cnt, buf);
+                        }
+                    }
                 }
             }
             pend_flush(E, cnt, buf);
         }
-      }
     }
 }
 
@@ -915,13 +995,22 @@ __device__ void dev_commit(const Eng& E, Smem& sm) {
         if (nun && !fits) atomicOr(&ctl->error, (unsigned)kErrListOverflow);
         // wide: a record and ceil(ng / 32) chunks of its own per unit
         const uint64_t wun = wide ? units : 0;
-        const uint64_t wck = wide ? (ng + kChunk - 1) / kChunk : 0;
+        // chunks of a wide unit: 32-group blocks times colour blocks (one
+        // colour per unfused unit)
+        const uint64_t ncb = E.unfused ? 1 : (bits + kColourBlock - 1) / kColourBlock;
+        const uint64_t wck = wide ? ((ng + kWideSpan - 1) / kWideSpan) * ncb : 0;
         const unsigned long long wgot =
             warp_alloc<unsigned long long>(&ctl->wide_packed, (unsigned long long)((wun * wck) << kUnitBits) | wun);
         const uint64_t wpos = wgot & kUnitMask, wc0 = wgot >> kUnitBits;
         const bool wfits = wide && wpos + wun <= E.list_cap && wc0 + wun * wck <= E.wide_chunk_cap;
-        if (wide && !wfits)
-            atomicOr(&ctl->error, (unsigned)(wpos + wun <= E.list_cap ? kErrChunkOverflow : kErrListOverflow));
+        if (wide && !wfits) {
+            if (wpos + wun <= E.list_cap) {
+                atomicOr(&ctl->error, (unsigned)kErrWideOverflow);
+                atomicMax(&ctl->wide_need, (unsigned long long)(wc0 + wun * wck));
+            } else {
+                atomicOr(&ctl->error, (unsigned)kErrListOverflow);
+            }
+        }
         if (wfits) {
             const uint64_t q0 = rs >> 2;
             const uint32_t masks = ((0xFu << (uint32_t)(rs & 3)) & 0xFu) | ((0xFu >> (3u - (uint32_t)((re - 1) & 3))) << 4);
@@ -1455,7 +1544,6 @@ __device__ void dev_schedule(const Eng& E, Smem& sm) {
         ctl->wide_packed = 0;
         ctl->wide_gnew = 0;
         ctl->wchunk_next = 0;
-        for (uint32_t k = 0; k < kWideQueues; ++k) ctl->wqueue[k * 32] = 0;
         atomicAdd(&ctl->st_units, (np & kUnitMask) + (wp & kUnitMask));
         const unsigned long long lg = h.list_groups + h.wide_groups;
         if (lg != 0) atomicAdd(h.dir == kDirPull ? &ctl->st_pull : &ctl->st_push, 1ull);
@@ -2010,6 +2098,19 @@ int grow_spill(Workspace* ws, uint64_t cap, cudaStream_t st) {
 }
 
 constexpr uint64_t kSpillMax = 1ull << 31;
+constexpr uint64_t kWideChunkMax = 0xFFFFFFFFull;
+
+// Replaces the wide-chunk map by one of `cap` entries.
+int grow_wide_chunks(Workspace* ws, uint64_t cap, cudaStream_t st) {
+    cudaStreamSynchronize(st);
+    cudaFree(ws->wide_chunk);
+    ws->wide_chunk = nullptr;
+    ws->wide_chunk_cap = cap;
+    size_t unused = 0;
+    const int rc = dalloc(&ws->wide_chunk, cap, unused);
+    if (rc != FBPT_OK) ws->wide_chunk_cap = 0;
+    return rc;
+}
 
 // Validates the arguments, gets the workspace and the output's fixed-size buffers.
 // force_wb (when not 0) sets the row width in words instead of the options:
@@ -2224,9 +2325,17 @@ int run_check(Run& r, fbpt_stats* stats, bool& again) {
     const Ctl* H = r.H;
     Workspace* ws = r.ws;
     if (H->error & kErrBarrierTimeout) return fail(FBPT_ETIMEOUT, "sampling run: a grid barrier wait gave up");
-    if (H->error == kErrSpillOverflow && ws->spill_cap < kSpillMax) {
-        // long RR sets outgrew the spill log: grow it and run again from a clean state
-        FBPT_TRY(grow_spill(ws, std::min<uint64_t>(ws->spill_cap * 8, kSpillMax), r.st));
+    const unsigned growable = kErrSpillOverflow | kErrWideOverflow;
+    if (H->error && (H->error & ~growable) == 0 &&
+        (!(H->error & kErrSpillOverflow) || ws->spill_cap < kSpillMax) &&
+        (!(H->error & kErrWideOverflow) || ws->wide_chunk_cap < kWideChunkMax)) {
+        // long RR sets outgrew the spill log, or many-colour units the wide-chunk
+        // map: grow what overflowed and run again from a clean state
+        if (H->error & kErrSpillOverflow)
+            FBPT_TRY(grow_spill(ws, std::min<uint64_t>(ws->spill_cap * 8, kSpillMax), r.st));
+        if (H->error & kErrWideOverflow)
+            FBPT_TRY(grow_wide_chunks(ws, std::min<uint64_t>(std::max<uint64_t>(2 * H->wide_need, 2 * ws->wide_chunk_cap),
+                                                             kWideChunkMax), r.st));
         FBPT_TRY(ws_zero(ws, r.st));
         if (stats) stats->overflow_reruns += 1;
         again = true;

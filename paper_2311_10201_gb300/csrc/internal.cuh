@@ -22,19 +22,20 @@ constexpr uint32_t kChunk = 32;         // 4-edge groups per expand chunk (one p
 // their expand chunks is 32 groups of that unit alone (the lanes share its
 // colours); narrower units are packed 32 groups per chunk across units.
 constexpr uint32_t kWideMin = 32;
+constexpr uint32_t kWideSpan = 64;      // groups of a wide chunk: two per lane
+#ifndef FBPT_COLOUR_BLOCK
+#define FBPT_COLOUR_BLOCK 32
+#endif
+// A wide chunk draws for at most this many of its unit's colours; a unit with
+// more colours has a chunk per (32 groups, block of colours), so that no chunk
+// holds a warp much longer than the others.
+constexpr uint32_t kColourBlock = FBPT_COLOUR_BLOCK;
 constexpr uint32_t kPendBuf = 32;       // per-warp buffer of new pending vertices in the expand
 #ifndef FBPT_CHUNKS_PER_GRAB
 #define FBPT_CHUNKS_PER_GRAB 2
 #endif
 constexpr uint32_t kChunksPerGrab = FBPT_CHUNKS_PER_GRAB;  // chunks a warp takes per atomic
-#ifndef FBPT_WIDE_QUEUES
-#define FBPT_WIDE_QUEUES 8
-#endif
-// The wide chunks of a level are split into this many contiguous ranges, each
-// with its own counter (on its own 128-byte line), so that the warps' grabs
-// do not all meet on one address; a warp starts on the range of its index and
-// moves on when a range runs out.
-constexpr uint32_t kWideQueues = FBPT_WIDE_QUEUES;
+
 
 enum ErrorBits : uint32_t {
     kErrListOverflow = 1u,
@@ -43,6 +44,7 @@ enum ErrorBits : uint32_t {
     kErrPendOverflow = 8u,
     kErrBarrierTimeout = 16u,
     kErrSpillOverflow = 32u,
+    kErrWideOverflow = 64u,   // the wide-chunk map was too small (the host grows it and reruns)
 };
 
 // How a level expands its frontier.
@@ -107,7 +109,7 @@ struct Ctl {
     unsigned long long wide_packed, wide_gnew;
     unsigned long long wide_units, wide_chunks, wide_groups;
     unsigned int wchunk_next, wpad;
-    unsigned int wqueue[kWideQueues * 32];  // wide-chunk counters, one per 128-byte line
+    unsigned long long wide_need;  // largest wide-chunk count a level asked for beyond the capacity
     // compaction of the coming level (fbpt_compaction); stage rows the scan
     // commit has handed out
     unsigned int mode, scan_rows;

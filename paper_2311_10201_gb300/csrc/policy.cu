@@ -170,13 +170,17 @@ __global__ void __launch_bounds__(256) k_mlp_grad(const float* __restrict__ P, c
 // One Adam step (Kingma and Ba, ICLR 2015, Algorithm 1: beta1 = 0.9, beta2 =
 // 0.999, eps = 1e-8) on the weights and biases; the input mean and scale
 // (the first 12 floats) are not trained.
+// The decay factors and their complements are each the float nearest to the
+// decimal constant (1 - 0.999f would be 1.3e-5 away from 0.001), and the bias
+// corrections 1 - beta^t are formed as -expm1(t log1p(-(1 - beta))), which
+// keeps their relative error at a few float ulps for every t.
 __global__ void k_adam(float* P, const float* grad, float* m, float* v, int t, float lr) {
-    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
-    const float c1 = 1.f - powf(b1, (float)t), c2 = 1.f - powf(b2, (float)t);
+    const float b1 = 0.9f, b2 = 0.999f, omb1 = 0.1f, omb2 = 0.001f, eps = 1e-8f;
+    const float c1 = -expm1f((float)t * log1pf(-omb1)), c2 = -expm1f((float)t * log1pf(-omb2));
     for (int i = kOffW1 + blockIdx.x * blockDim.x + threadIdx.x; i < kNP; i += gridDim.x * blockDim.x) {
         const float gi = grad[i];
-        const float mi = b1 * m[i] + (1.f - b1) * gi;
-        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        const float mi = b1 * m[i] + omb1 * gi;
+        const float vi = b2 * v[i] + omb2 * gi * gi;
         m[i] = mi;
         v[i] = vi;
         P[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);

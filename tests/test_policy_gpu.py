@@ -79,8 +79,11 @@ def test_gpu_adam_step_matches_the_oracle(fbpt):
         rp, rm, rv = mlp.adam_step(P.astype(np.float64), g.astype(np.float64), M.astype(np.float64),
                                    V.astype(np.float64), t, lr=lr)
         k = slice(2 * mlp.N_IN, None)  # the trained weights and biases (mean and scale keep no moments)
-        assert np.allclose(M2[k], rm[k], rtol=2e-6, atol=1e-12), t
-        assert np.allclose(V2[k], rv[k], rtol=2e-6, atol=1e-15), t
+        # m is a sum of two terms that may cancel: the FP32 error bound is
+        # relative to the terms, not to the result
+        mtol = 4 * np.finfo(np.float32).eps * (0.9 * np.abs(M[k]) + 0.1 * np.abs(g[k])) + 1e-30
+        assert np.all(np.abs(M2[k] - rm[k]) <= mtol), t
+        assert np.allclose(V2[k], rv[k], rtol=2e-6, atol=1e-30), t
         tol = 4 * np.finfo(np.float32).eps * np.abs(rp) + 1e-5 * lr
         assert np.all(np.abs(P2 - rp) <= tol), (t, float(np.max(np.abs(P2 - rp) - tol)))
         assert np.array_equal(P2[:2 * mlp.N_IN], P[:2 * mlp.N_IN])  # input mean and scale untouched
@@ -108,9 +111,10 @@ def test_scheduler_features_and_decisions_match_the_oracle(fbpt, case):
     oracle/mlp.py features of the row's own counts, rounded to float32 (at most
     1 ulp apart).  Inference: the device outputs equal the FP64 forward pass of
     the shipped parameters on those features to FP32 tolerance, and the level
-    ran in the direction the oracle's predict_action picks over the allowed
-    set (push, filtered push, and pull when the row width allows it), except
-    where the two best allowed outputs lie within that tolerance."""
+    ran with the action the oracle's predict_action picks over the allowed
+    set (push and filtered push with either compaction, and pull when the row
+    width allows it), except where the two best allowed outputs lie within
+    that tolerance."""
     import synth
     if case == "er_1k":
         w = synth.er_1k()
@@ -134,9 +138,11 @@ def test_scheduler_features_and_decisions_match_the_oracle(fbpt, case):
     out_dev = rows["outputs"].astype(np.float64)
     tol = 1e-4 * (1.0 + np.abs(out_ref))
     assert np.all(np.abs(out_dev - out_ref) <= tol)
-    allowed = (0, 1, 2) if pull else (0, 1)
+    # actions: push, filtered, pull (queue), push, filtered (scan)
+    allowed = (0, 1, 2, 3, 4) if pull else (0, 1, 3, 4)
     want = mlp.predict_action(p.astype(np.float32).astype(np.float64), X_dev.astype(np.float64), allowed)
-    got = rows["direction"].astype(np.int64)
+    d = rows["direction"].astype(np.int64)
+    got = d + 3 * ((rows["compaction"] == 1) & (d != 2)).astype(np.int64)
     o = out_ref[:, list(allowed)]
     srt = np.sort(o, axis=1)
     close = (srt[:, 1] - srt[:, 0]) <= 2e-4 * (1.0 + np.abs(srt[:, 0]))
@@ -235,3 +241,56 @@ def test_policy_file_round_trip(fbpt, tmp_path):
     assert np.array_equal(q.params(), ref)
     p.close()
     q.close()
+
+
+# ---- the row-width head (outputs 5..7) ---------------------------------------------------
+
+WIDTHS = (4, 16, 64)
+
+
+@pytest.mark.parametrize("case", ["er_2k", "rmat15_p01", "rmat17_wc"])
+def test_policy_width_matches_the_oracle(fbpt, case):
+    """fbpt_policy_width's scores are the means, over the probe's levels with a
+    frontier, of outputs 5..7 of the FP64 forward pass on the device features
+    of that probe (rerun here with the same shape and trace on), and its width
+    is the one with the smallest mean."""
+    g, seed, S, _ = {w[0].name: w for w in held_out_workloads()}[
+        {"er_2k": "er-2k", "rmat15_p01": "rmat15-p0.1", "rmat17_wc": "rmat-s17-ef16-wc"}[case]]
+    dg = fbpt.Graph.from_synth(g)
+    words, scores = fbpt.policy_width(dg, seed, S)
+    tr = fbpt.sample(dg, seed, 0, min(S, 8192), words=8, slots=1, refill="lane", schedule="learned",
+                     launch="graph", trace_cap=1 << 16).trace
+    dg.close()
+    rows = tr[1:][tr[1:]["units"] > 0]
+    p = np.loadtxt(fbpt.DEFAULT_POLICY_FILE, dtype=np.float64).astype(np.float32).astype(np.float64)
+    out, _ = mlp.forward(p, rows["features"].astype(np.float64))
+    want = out[:, 5:8].mean(0)
+    assert np.allclose(scores, want, rtol=1e-4, atol=1e-4)
+    assert words == WIDTHS[int(np.argmin(scores))]
+
+
+def test_policy_width_against_the_autotuner(fbpt):
+    """The width the network picks from one probe, against the width the
+    autotuner measures among 1 .. 64 words: the rate of each at full size, on
+    the held-out graphs (reported; the assertion only rules out a pick far
+    from the measured best)."""
+    import torch
+    rows = []
+    for g, seed, S, _ in held_out_workloads():
+        S = max(S, 16384)
+        dg = fbpt.Graph.from_synth(g)
+        pw, _ = fbpt.policy_width(dg, seed, S)
+        tw = fbpt.autotune(dg, seed, S, schedule="push")
+        tw_words = tw["words"] * tw["slots"]
+
+        def rate(wb):
+            kw = dict(words=min(wb, 8), slots=max(wb // 8, 1), refill="lane", schedule="push", launch="graph")
+            fbpt.sample(dg, seed, 0, S, **kw)
+            torch.cuda.synchronize()
+            return S / (1e-3 * fbpt.sample(dg, seed, 0, S, **kw).stats.ms_total)
+        r_policy, r_tuner = rate(pw), rate(tw_words)
+        dg.close()
+        rows.append((g.name, pw, tw_words, r_policy, r_tuner))
+        print(f"{g.name}: policy {pw} words {r_policy:.0f}/s, autotuner {tw_words} words {r_tuner:.0f}/s "
+              f"({r_policy / r_tuner:.2f}x)")
+        assert r_policy >= 0.5 * r_tuner
