@@ -310,20 +310,18 @@ __device__ __forceinline__ void pend_flush(const Eng& E, uint32_t* cnt, uint32_t
     __syncwarp();
 }
 
-// Colours y of word i reach w: next[w][i] |= y.  Queue compaction: w becomes
-// pending (once per level) when the first word of next[w] turns non-zero.
-// Scan compaction: only the bits are set (reductions, no returned value); the
-// commit finds w by its word-occupancy mask.
+// Colours y of word i reach w: next[w][i] |= y and bit i of nocc[w] is set,
+// both as reductions that return nothing.  Queue compaction: the nocc update
+// returns the old mask instead, and w becomes pending (once per level) when it
+// was zero, i.e. on the level's first live edge into w.  Scan compaction: the
+// commit finds w by its non-zero nocc mask.
 __device__ __forceinline__ void push_live(const Eng& E, uint32_t w, uint32_t i, uint64_t y, bool scan, uint32_t* cnt,
                                           uint32_t* buf) {
+    atomicOr((unsigned long long*)&E.next[(uint64_t)w * E.WB + i], (unsigned long long)y);
     if (scan) {
-        atomicOr((unsigned long long*)&E.next[(uint64_t)w * E.WB + i], (unsigned long long)y);
         atomicOr((unsigned long long*)&E.nocc[w], 1ull << i);
         return;
     }
-    const unsigned long long old =
-        atomicOr((unsigned long long*)&E.next[(uint64_t)w * E.WB + i], (unsigned long long)y);
-    if (old != 0) return;
     if (atomicOr((unsigned long long*)&E.nocc[w], 1ull << i) != 0) return;
     pend_push(E, cnt, buf, w);
 }
@@ -349,7 +347,7 @@ __device__ __forceinline__ uint32_t draw_edges(const uint4& T, uint32_t sure) {
 // has is not sent to it (and needs no draw if every source has it).
 template <bool filtered>
 __device__ __forceinline__ void group_draws(const Eng& E, const uint32_t* lj, uint64_t x, uint32_t i, uint64_t q,
-                                            const uint4& T, uint32_t sure, const PhiloxKeys& K,
+                                            const uint4& c4, const uint4& T, uint32_t sure, const PhiloxKeys& K,
                                             const uint64_t (&vis)[4], bool scan, uint32_t* cnt, uint32_t* buf) {
     const uint32_t f_lo = (uint32_t)E.first_id, f_hi = (uint32_t)(E.first_id >> 32);
     const uint32_t qlo = (uint32_t)q, qhi = (uint32_t)(q >> 32);
@@ -380,7 +378,6 @@ __device__ __forceinline__ void group_draws(const Eng& E, const uint32_t* lj, ui
             z3 &= ~(uint32_t)(vis[3] >> (32 * h));
         }
         if (z0 | z1 | z2 | z3) {
-            const uint4 c4 = __ldg(reinterpret_cast<const uint4*>(E.col) + q);
             if (z0) push_live(E, c4.x, i, (uint64_t)z0 << (32 * h), scan, cnt, buf);
             if (z1) push_live(E, c4.y, i, (uint64_t)z1 << (32 * h), scan, cnt, buf);
             if (z2) push_live(E, c4.z, i, (uint64_t)z2 << (32 * h), scan, cnt, buf);
@@ -412,8 +409,9 @@ __device__ __forceinline__ void source_visited(const Eng& E, uint64_t q, uint32_
 // the colours x of word i: two independent Philox chains per colour, sharing
 // the colour's sample id; live colours gathered per half-word and edge.
 __device__ __forceinline__ void pair_draws(const Eng& E, const uint32_t* lj, uint64_t x, uint32_t i, uint64_t q,
-                                           const uint4& Ta, uint32_t sa, const uint4& Tb, uint32_t sb,
-                                           const PhiloxKeys& K, bool scan, uint32_t* cnt, uint32_t* buf) {
+                                           const uint4& ca, const uint4& Ta, uint32_t sa, const uint4& cb,
+                                           const uint4& Tb, uint32_t sb, const PhiloxKeys& K, bool scan,
+                                           uint32_t* cnt, uint32_t* buf) {
     const uint32_t f_lo = (uint32_t)E.first_id, f_hi = (uint32_t)(E.first_id >> 32);
     const uint64_t qb = q + kChunk;
     const uint32_t qalo = (uint32_t)q, qahi = (uint32_t)(q >> 32), qblo = (uint32_t)qb, qbhi = (uint32_t)(qb >> 32);
@@ -445,18 +443,16 @@ __device__ __forceinline__ void pair_draws(const Eng& E, const uint32_t* lj, uin
             }
         }
         if (a0 | a1 | a2 | a3) {
-            const uint4 c4 = __ldg(reinterpret_cast<const uint4*>(E.col) + q);
-            if (a0) push_live(E, c4.x, i, (uint64_t)a0 << (32 * h), scan, cnt, buf);
-            if (a1) push_live(E, c4.y, i, (uint64_t)a1 << (32 * h), scan, cnt, buf);
-            if (a2) push_live(E, c4.z, i, (uint64_t)a2 << (32 * h), scan, cnt, buf);
-            if (a3) push_live(E, c4.w, i, (uint64_t)a3 << (32 * h), scan, cnt, buf);
+            if (a0) push_live(E, ca.x, i, (uint64_t)a0 << (32 * h), scan, cnt, buf);
+            if (a1) push_live(E, ca.y, i, (uint64_t)a1 << (32 * h), scan, cnt, buf);
+            if (a2) push_live(E, ca.z, i, (uint64_t)a2 << (32 * h), scan, cnt, buf);
+            if (a3) push_live(E, ca.w, i, (uint64_t)a3 << (32 * h), scan, cnt, buf);
         }
         if (b0 | b1 | b2 | b3) {
-            const uint4 c4 = __ldg(reinterpret_cast<const uint4*>(E.col) + qb);
-            if (b0) push_live(E, c4.x, i, (uint64_t)b0 << (32 * h), scan, cnt, buf);
-            if (b1) push_live(E, c4.y, i, (uint64_t)b1 << (32 * h), scan, cnt, buf);
-            if (b2) push_live(E, c4.z, i, (uint64_t)b2 << (32 * h), scan, cnt, buf);
-            if (b3) push_live(E, c4.w, i, (uint64_t)b3 << (32 * h), scan, cnt, buf);
+            if (b0) push_live(E, cb.x, i, (uint64_t)b0 << (32 * h), scan, cnt, buf);
+            if (b1) push_live(E, cb.y, i, (uint64_t)b1 << (32 * h), scan, cnt, buf);
+            if (b2) push_live(E, cb.z, i, (uint64_t)b2 << (32 * h), scan, cnt, buf);
+            if (b3) push_live(E, cb.w, i, (uint64_t)b3 << (32 * h), scan, cnt, buf);
         }
     }
 }
@@ -496,9 +492,16 @@ __device__ __forceinline__ void expand_wide(const Eng& E, const uint32_t* lane_j
             if (gl == 0) vma &= rb.w & 0xFu;
             if (gl + 1 == rb.x) vma &= (rb.w >> 4) & 0xFu;
             if (gl + kChunk + 1 == rb.x) vmb &= (rb.w >> 4) & 0xFu;
-            uint4 ta = make_uint4(0u, 0u, 0u, 0u), tb = ta;
-            if (vma) ta = __ldg(thr4 + q);
-            if (vmb) tb = __ldg(thr4 + q + kChunk);
+            uint4 ta = make_uint4(0u, 0u, 0u, 0u), tb = ta, ca = ta, cbv = ta;
+            const uint4* col4 = reinterpret_cast<const uint4*>(E.col);
+            if (vma) {
+                ta = __ldg(thr4 + q);
+                ca = __ldg(col4 + q);
+            }
+            if (vmb) {
+                tb = __ldg(thr4 + q + kChunk);
+                cbv = __ldg(col4 + q + kChunk);
+            }
             uint4 Ta, Tb;
             const uint32_t sa = group_thresholds(vma, ta, Ta), sb = group_thresholds(vmb, tb, Tb);
             if (cb == 0) n_edges += __popc(vma) + __popc(vmb);
@@ -523,8 +526,8 @@ __device__ __forceinline__ void expand_wide(const Eng& E, const uint32_t* lane_j
                     take -= __popcll(x);
                     n_calls += (uint64_t)need * __popcll(x);
                     if (!filtered) {
-                        pair_draws(E, lane_j + (i << 6), (any_a || any_b) ? x : 0ull, i, q, Ta, sa, Tb, sb, K, scan,
-                                   cnt, buf);
+                        pair_draws(E, lane_j + (i << 6), (any_a || any_b) ? x : 0ull, i, q, ca, Ta, sa, cbv, Tb, sb, K,
+                                   scan, cnt, buf);
                     } else {
 #pragma unroll 1
                         for (int g2 = 0; g2 < 2; ++g2) {
@@ -533,8 +536,8 @@ __device__ __forceinline__ void expand_wide(const Eng& E, const uint32_t* lane_j
                             uint64_t vis[4] = {~0ull, ~0ull, ~0ull, ~0ull};
                             if (vm) source_visited(E, qq, vm, i, vis);
                             const uint64_t xs = (g2 ? any_b : any_a) ? x & ~(vis[0] & vis[1] & vis[2] & vis[3]) : 0ull;
-                            group_draws<true>(E, lane_j + (i << 6), xs, i, qq, g2 ? Tb : Ta, g2 ? sb : sa, K, vis,
-                                              scan, cnt, buf);
+                            group_draws<true>(E, lane_j + (i << 6), xs, i, qq, g2 ? cbv : ca, g2 ? Tb : Ta,
+                                              g2 ? sb : sa, K, vis, scan, cnt, buf);
                         }
                     }
                 }
@@ -549,7 +552,7 @@ __device__ __forceinline__ void expand_wide(const Eng& E, const uint32_t* lane_j
 // unit among the chunk's (at most 32) units.
 struct Grp {
     uint64_t q, occ;
-    uint4 T;
+    uint4 c4, T;
     uint32_t mrow, only, sure, vm;
 };
 
@@ -561,6 +564,7 @@ __device__ __forceinline__ bool grp_load(const Eng& E, uint32_t u, uint64_t j, G
     G.only = E.unfused ? LD<ro>(&E.list_only[u]) : 0u;
     G.q = (rs >> 2) + j;
     const uint4 t = __ldg(reinterpret_cast<const uint4*>(E.thr) + G.q);
+    G.c4 = __ldg(reinterpret_cast<const uint4*>(E.col) + G.q);
     const uint32_t first = j == 0 ? (uint32_t)(rs & 3) : 0u;
     const uint32_t last = G.q == ((re - 1) >> 2) ? (uint32_t)((re - 1) & 3) : 3u;
     G.vm = (0xFu << first) & (0xFu >> (3u - last));
@@ -585,7 +589,7 @@ __device__ __forceinline__ void grp_run(const Eng& E, const uint32_t* lane_j, co
             if (!x) continue;
         }
         if (need) n_calls += __popcll(x);
-        group_draws<filtered>(E, lane_j + (i << 6), x, i, G.q, G.T, G.sure, K, vis, scan, cnt, buf);
+        group_draws<filtered>(E, lane_j + (i << 6), x, i, G.q, G.c4, G.T, G.sure, K, vis, scan, cnt, buf);
     }
 }
 
