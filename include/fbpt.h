@@ -388,8 +388,10 @@ int fbpt_select_seeds_noalloc(const fbpt_rrsets* rr, uint32_t k, uint32_t* seeds
  * extended, never redrawn); greedy picks k seeds covering a fraction F of
  * them; if n F >= (1 + eps') x the lower bound is LB = n F / (1 + eps') and
  * the rounds stop (LB = 1 if no round succeeds).  Then theta =
- * ceil(lambda* / LB), the sample is extended to max(its size, theta) and the
- * greedy seeds over it are the result.  Every sampling step is fbpt_sample
+ * ceil(lambda* / LB), theta RR sets are drawn afresh (sample ids right after
+ * those of the estimation rounds: Chen, 2018, showed that reusing the
+ * estimation sets, as the original IMM does, breaks the martingale argument
+ * behind the guarantee) and the greedy seeds over them are the result.  Every sampling step is fbpt_sample
  * with opts, every selection fbpt_select_seeds.
  *
  * Needs n >= 2, 1 <= k <= n, epsilon > 0, ell > 0.  max_samples (0 = none)
@@ -399,7 +401,8 @@ int fbpt_select_seeds_noalloc(const fbpt_rrsets* rr, uint32_t k, uint32_t* seeds
  * accumulates over every sampling call. */
 typedef struct fbpt_imm_result {
     uint64_t theta;       /* ceil(lambda* / LB) */
-    uint64_t samples;     /* RR sets the final selection used: max(theta, the last round's theta_i) */
+    uint64_t samples;     /* RR sets the final selection used (theta) */
+    uint64_t first_final_id; /* sample id of the first of them (the estimation sample's size) */
     double lower_bound;   /* LB */
     double coverage;      /* fraction of those RR sets the seeds cover */
     double lambda_prime, lambda_star;

@@ -11,7 +11,10 @@ step.  Readings (also stated in include/fbpt.h, fbpt_imm):
   - the estimation rounds are i = 1 .. ceil(log2 n) - 1;
   - each round extends the sample to ceil(lambda' / x) RR sets (sample ids
     0, 1, ... under one seed; earlier sets are kept, never redrawn);
-  - theta = ceil(lambda* / LB); the final sample has max(its size, theta) sets.
+  - theta = ceil(lambda* / LB); the final selection runs over theta RR sets
+    drawn afresh (sample ids after those of the estimation rounds): Chen
+    (2018) showed that reusing the estimation sets, as the original IMM does,
+    breaks the martingale argument behind the guarantee.
 """
 from __future__ import annotations
 
@@ -88,8 +91,8 @@ def imm(g, k: int, epsilon: float, ell: float, seed: int):
             LB = n * F / (1.0 + epsp)
             break
     theta = math.ceil(lam_s / LB)
-    R.extend(theta)
-    seeds, gains = greedy(n, R.rr(), k)
-    info = {"theta": theta, "samples": R.size, "lower_bound": LB, "coverage": int(gains.sum()) / R.size,
-            "lambda_prime": lam_p, "lambda_star": lam_s, "rounds": rounds}
+    final = rr_sets(g, seed, R.size, theta)
+    seeds, gains = greedy(n, final, k)
+    info = {"theta": theta, "samples": theta, "lower_bound": LB, "coverage": int(gains.sum()) / theta,
+            "lambda_prime": lam_p, "lambda_star": lam_s, "rounds": rounds, "first_final_id": R.size}
     return seeds, gains, info

@@ -53,7 +53,8 @@ class Tuning(ctypes.Structure):
 
 
 class ImmResult(ctypes.Structure):
-    _fields_ = [("theta", ctypes.c_uint64), ("samples", ctypes.c_uint64), ("lower_bound", ctypes.c_double),
+    _fields_ = [("theta", ctypes.c_uint64), ("samples", ctypes.c_uint64), ("first_final_id", ctypes.c_uint64),
+                ("lower_bound", ctypes.c_double),
                 ("coverage", ctypes.c_double), ("lambda_prime", ctypes.c_double), ("lambda_star", ctypes.c_double),
                 ("rounds", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 

@@ -42,6 +42,9 @@ namespace fbpt {
 namespace {
 
 constexpr int kThreads = 256;
+// dynamic shared memory of the expand kernels: two slots per warp of 32 lanes x
+// four 16-byte vectors (the next wide chunk's thresholds and sources)
+constexpr size_t kStageBytes = (kThreads / 32) * 2 * 32 * 4 * sizeof(uint4);
 #ifndef FBPT_EXPAND_ILP
 #define FBPT_EXPAND_ILP 1   // chunks a warp works on at once in the expand
 #endif
@@ -457,60 +460,128 @@ __device__ __forceinline__ void pair_draws(const Eng& E, const uint32_t* lj, uin
     }
 }
 
+// Asynchronous 16-byte global -> shared copies (no register holds the data).
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Where chunk c of wide unit (ra, rb) puts this lane: its two groups q and
+// q + 32 with their in-row edge masks, and the chunk's colour block.
+struct WidePos {
+    uint64_t q;
+    uint32_t vma, vmb, cb;
+};
+__device__ __forceinline__ WidePos wide_pos(uint32_t c, const uint4& ra, const uint4& rb, uint32_t lane) {
+    WidePos p;
+    const uint32_t r = c - rb.y, ngb = (rb.x + kWideSpan - 1) / kWideSpan;
+    uint32_t gb = r;
+    p.cb = 0;
+    if (r >= ngb) {
+        p.cb = r / ngb;
+        gb = r - p.cb * ngb;
+    }
+    const uint32_t gl = kWideSpan * gb + lane;
+    p.q = (((uint64_t)ra.y << 32) | ra.x) + gl;
+    p.vma = gl < rb.x ? 0xFu : 0u;
+    p.vmb = gl + kChunk < rb.x ? 0xFu : 0u;
+    if (gl == 0) p.vma &= rb.w & 0xFu;
+    if (gl + 1 == rb.x) p.vma &= (rb.w >> 4) & 0xFu;
+    if (gl + kChunk + 1 == rb.x) p.vmb &= (rb.w >> 4) & 0xFu;
+    return p;
+}
+
 // Wide units: a chunk is kWideSpan consecutive groups of ONE unit (lane l
 // takes groups l and l + 32 of it), times a block of at most kColourBlock of
 // the unit's colours, so the unit record, its colour words and each draw's
-// colour are warp-uniform.
+// colour are warp-uniform.  A warp's first grab is static (warp index), later
+// ones come from the level's counter.  While a chunk draws, the threshold and
+// source vectors of the next chunk of the grab, when it belongs to the same
+// unit, travel into one of the warp's two shared-memory slots (stage: 2 x 32
+// lanes x 4 vectors; the slot a chunk reads is never the one being filled).
 template <bool filtered, bool ro>
 __device__ __forceinline__ void expand_wide(const Eng& E, const uint32_t* lane_j, const PhiloxKeys& K, uint64_t NC,
-                                            bool scan, uint32_t* cnt, uint32_t* buf, uint64_t& n_edges,
-                                            uint64_t& n_calls) {
+                                            bool scan, uint32_t* cnt, uint32_t* buf, uint4* stage,
+                                            uint64_t& n_edges, uint64_t& n_calls) {
     Ctl* ctl = E.ctl;
     const uint32_t lane = lane_id();
     const uint4* thr4 = reinterpret_cast<const uint4*>(E.thr);
-    for (;;) {
+    const uint4* col4 = reinterpret_cast<const uint4*>(E.col);
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    const uint32_t wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    uint32_t sl = 0;  // slot holding the current chunk's vectors (when pre)
+    for (uint32_t grab = 0;; ++grab) {
         uint32_t c0 = 0;
-        if (lane == 0) c0 = atomicAdd(&ctl->wchunk_next, kChunksPerGrab);
-        c0 = __shfl_sync(0xffffffffu, c0, 0);
+        if (grab == 0) {
+            c0 = wid * kChunksPerGrab;
+        } else {
+            if (lane == 0) c0 = nwarps * kChunksPerGrab + atomicAdd(&ctl->wchunk_next, kChunksPerGrab);
+            c0 = __shfl_sync(0xffffffffu, c0, 0);
+        }
         if (c0 >= NC) break;
         const uint32_t c1 = (uint32_t)min((uint64_t)c0 + kChunksPerGrab, NC);
+        uint32_t u = 0xFFFFFFFFu;
+        uint4 ra = make_uint4(0u, 0u, 0u, 0u), rb = ra;
+        bool pre = false;  // this chunk's vectors are in the slot
         for (uint32_t c = c0; c < c1; ++c) {
-            const uint32_t u = LD<ro>(&E.wide_chunk[c]);
-            const uint4 ra = LD<ro>(&E.wide_rec[2ull * u]);
-            const uint4 rb = LD<ro>(&E.wide_rec[2ull * u + 1]);
-            // chunk r of the unit: group block gb, colour block cb
-            const uint32_t r = c - rb.y, ngb = (rb.x + kWideSpan - 1) / kWideSpan;
-            uint32_t gb = r, cb = 0;
-            if (r >= ngb) {
-                cb = r / ngb;
-                gb = r - cb * ngb;
+            const uint32_t uc = LD<ro>(&E.wide_chunk[c]);
+            if (uc != u) {
+                u = uc;
+                ra = LD<ro>(&E.wide_rec[2ull * u]);
+                rb = LD<ro>(&E.wide_rec[2ull * u + 1]);
             }
-            const uint32_t gl = kWideSpan * gb + lane;
-            const uint64_t q = (((uint64_t)ra.y << 32) | ra.x) + gl;
-            // in-row edges of the lane's two groups
-            uint32_t vma = gl < rb.x ? 0xFu : 0u, vmb = gl + kChunk < rb.x ? 0xFu : 0u;
-            if (gl == 0) vma &= rb.w & 0xFu;
-            if (gl + 1 == rb.x) vma &= (rb.w >> 4) & 0xFu;
-            if (gl + kChunk + 1 == rb.x) vmb &= (rb.w >> 4) & 0xFu;
+            const WidePos P = wide_pos(c, ra, rb, lane);
             uint4 ta = make_uint4(0u, 0u, 0u, 0u), tb = ta, ca = ta, cbv = ta;
-            const uint4* col4 = reinterpret_cast<const uint4*>(E.col);
-            if (vma) {
-                ta = __ldg(thr4 + q);
-                ca = __ldg(col4 + q);
+            if (pre) {
+                cp_async_wait_all();
+                const uint4* slot = stage + (sl * 32 + lane) * 4;
+                if (P.vma) {
+                    ta = slot[0];
+                    ca = slot[1];
+                }
+                if (P.vmb) {
+                    tb = slot[2];
+                    cbv = slot[3];
+                }
+            } else {
+                if (P.vma) {
+                    ta = __ldg(thr4 + P.q);
+                    ca = __ldg(col4 + P.q);
+                }
+                if (P.vmb) {
+                    tb = __ldg(thr4 + P.q + kChunk);
+                    cbv = __ldg(col4 + P.q + kChunk);
+                }
             }
-            if (vmb) {
-                tb = __ldg(thr4 + q + kChunk);
-                cbv = __ldg(col4 + q + kChunk);
+            // the next chunk of the grab, if it continues this unit: its vectors
+            // head for the slot while this chunk draws
+            pre = false;
+            if (c + 1 < c1 && LD<ro>(&E.wide_chunk[c + 1]) == u) {
+                sl ^= 1u;
+                uint4* slot = stage + (sl * 32 + lane) * 4;
+                const WidePos Pn = wide_pos(c + 1, ra, rb, lane);
+                if (Pn.vma) {
+                    cp_async16(&slot[0], thr4 + Pn.q);
+                    cp_async16(&slot[1], col4 + Pn.q);
+                }
+                if (Pn.vmb) {
+                    cp_async16(&slot[2], thr4 + Pn.q + kChunk);
+                    cp_async16(&slot[3], col4 + Pn.q + kChunk);
+                }
+                cp_async_commit();
+                pre = true;
             }
             uint4 Ta, Tb;
-            const uint32_t sa = group_thresholds(vma, ta, Ta), sb = group_thresholds(vmb, tb, Tb);
-            if (cb == 0) n_edges += __popc(vma) + __popc(vmb);
+            const uint32_t sa = group_thresholds(P.vma, ta, Ta), sb = group_thresholds(P.vmb, tb, Tb);
+            if (P.cb == 0) n_edges += __popc(P.vma) + __popc(P.vmb);
             const uint32_t need = (draw_edges(Ta, sa) != 0u ? 1u : 0u) + (draw_edges(Tb, sb) != 0u ? 1u : 0u);
             const bool any_a = (Ta.x | Ta.y | Ta.z | Ta.w) != 0u, any_b = (Tb.x | Tb.y | Tb.z | Tb.w) != 0u;
             if (__any_sync(0xffffffffu, any_a || any_b)) {
                 uint64_t words = ((uint64_t)ra.w << 32) | ra.z;
                 // the unit's colours in (word, bit) order: skip cb blocks, take one
-                uint32_t skip = cb * kColourBlock, take = kColourBlock;
+                uint32_t skip = P.cb * kColourBlock, take = kColourBlock;
                 while (words && take) {
                     const uint32_t i = __ffsll((long long)words) - 1;
                     words &= words - 1;
@@ -526,13 +597,13 @@ __device__ __forceinline__ void expand_wide(const Eng& E, const uint32_t* lane_j
                     take -= __popcll(x);
                     n_calls += (uint64_t)need * __popcll(x);
                     if (!filtered) {
-                        pair_draws(E, lane_j + (i << 6), (any_a || any_b) ? x : 0ull, i, q, ca, Ta, sa, cbv, Tb, sb, K,
-                                   scan, cnt, buf);
+                        pair_draws(E, lane_j + (i << 6), (any_a || any_b) ? x : 0ull, i, P.q, ca, Ta, sa, cbv, Tb, sb,
+                                   K, scan, cnt, buf);
                     } else {
 #pragma unroll 1
                         for (int g2 = 0; g2 < 2; ++g2) {
-                            const uint32_t vm = g2 ? vmb : vma;
-                            const uint64_t qq = g2 ? q + kChunk : q;
+                            const uint32_t vm = g2 ? P.vmb : P.vma;
+                            const uint64_t qq = g2 ? P.q + kChunk : P.q;
                             uint64_t vis[4] = {~0ull, ~0ull, ~0ull, ~0ull};
                             if (vm) source_visited(E, qq, vm, i, vis);
                             const uint64_t xs = (g2 ? any_b : any_a) ? x & ~(vis[0] & vis[1] & vis[2] & vis[3]) : 0ull;
@@ -544,6 +615,7 @@ __device__ __forceinline__ void expand_wide(const Eng& E, const uint32_t* lane_j
             }
             pend_flush(E, cnt, buf);
         }
+        if (pre) cp_async_wait_all();  // nothing may still be landing in the slot
     }
 }
 
@@ -775,7 +847,7 @@ __device__ __forceinline__ void expand_lt(const Eng& E, const uint32_t* lane_j, 
 enum ExpandPart : int { kPartPush = 0, kPartAlt = 1, kPartAll = 2 };
 
 template <int part>
-__device__ void dev_expand(const Eng& E, uint32_t* lane_j, uint32_t* pcnt, uint32_t* pbuf) {
+__device__ void dev_expand(const Eng& E, uint32_t* lane_j, uint32_t* pcnt, uint32_t* pbuf, uint4* pstage) {
     Ctl* ctl = E.ctl;
     const uint64_t G = L2(&ctl->list_groups);
     const uint64_t NW = L2(&ctl->wide_chunks);
@@ -794,6 +866,7 @@ __device__ void dev_expand(const Eng& E, uint32_t* lane_j, uint32_t* pcnt, uint3
     const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
     uint32_t* cnt = pcnt + warp;
     uint32_t* buf = pbuf + warp * kPendBuf;
+    uint4* wstage = pstage + warp * 2 * 32 * 4;
     if (lane == 0) *cnt = 0;
     __syncthreads();
 #ifdef FBPT_KEYS_COMPUTED
@@ -815,10 +888,10 @@ __device__ void dev_expand(const Eng& E, uint32_t* lane_j, uint32_t* pcnt, uint3
     } else if (part != kPartPush && pull) {
         dev_pull(E, lane_j, K, n_edges, n_calls);
     } else if (part != kPartPush && dir == kDirFiltered) {
-        expand_wide<true, part != kPartAll>(E, lane_j, K, NW, scan, cnt, buf, n_edges, n_calls);
+        expand_wide<true, part != kPartAll>(E, lane_j, K, NW, scan, cnt, buf, wstage, n_edges, n_calls);
         expand_push<true, part != kPartAll>(E, lane_j, K, G, U, nchunks, scan, cnt, buf, n_edges, n_calls);
     } else if (part != kPartAlt) {
-        expand_wide<false, part != kPartAll>(E, lane_j, K, NW, scan, cnt, buf, n_edges, n_calls);
+        expand_wide<false, part != kPartAll>(E, lane_j, K, NW, scan, cnt, buf, wstage, n_edges, n_calls);
         expand_push<false, part != kPartAll>(E, lane_j, K, G, U, nchunks, scan, cnt, buf, n_edges, n_calls);
     }
     n_edges = warp_sum(n_edges);
@@ -1588,12 +1661,14 @@ __global__ void __launch_bounds__(kThreads) k_sweep(const Eng E) {
 __global__ void __launch_bounds__(kThreads, FBPT_EXPAND_MINB) k_expand(const Eng E) {
     __shared__ uint32_t lane_j[kMaxLanes];
     __shared__ uint32_t pcnt[kThreads / 32], pbuf[kThreads / 32 * kPendBuf];
-    dev_expand<kPartPush>(E, lane_j, pcnt, pbuf);
+    extern __shared__ uint4 pstage[];  // kStageBytes, dynamic
+    dev_expand<kPartPush>(E, lane_j, pcnt, pbuf, pstage);
 }
 __global__ void __launch_bounds__(kThreads) k_expand_alt(const Eng E) {
     __shared__ uint32_t lane_j[kMaxLanes];
     __shared__ uint32_t pcnt[kThreads / 32], pbuf[kThreads / 32 * kPendBuf];
-    dev_expand<kPartAlt>(E, lane_j, pcnt, pbuf);
+    extern __shared__ uint4 pstage[];  // kStageBytes, dynamic
+    dev_expand<kPartAlt>(E, lane_j, pcnt, pbuf, pstage);
 }
 __global__ void __launch_bounds__(kThreads) k_commit(const Eng E) {
     __shared__ Smem sm;
@@ -1652,12 +1727,13 @@ __device__ bool grid_barrier(const Eng& E, Smem& sm, unsigned& gen, bool schedul
 
 __global__ void __launch_bounds__(kThreads) k_run(const Eng E) {
     __shared__ Smem sm;
+    extern __shared__ uint4 pstage[];  // kStageBytes, dynamic: the expand's per-warp slots
     Ctl* ctl = E.ctl;
     unsigned gen = 0;
     for (;;) {
         dev_sweep(E, sm.lane, sm.fin);  // lanes finished at the previous level
         dev_init(E);       // lanes given a sample at the previous level
-        dev_expand<kPartAll>(E, sm.lane, sm.pcnt, sm.pbuf);
+        dev_expand<kPartAll>(E, sm.lane, sm.pcnt, sm.pbuf, pstage);
         if (!grid_barrier(E, sm, gen, false)) return;
         dev_commit(E, sm);
         if (!grid_barrier(E, sm, gen, true)) return;
@@ -1801,10 +1877,13 @@ LaunchShape launch_shape() {
     if (!done) {
         const int sms = device_sm_count();
         int per = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_expand, kThreads, 0);
+        cudaFuncSetAttribute(k_expand, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStageBytes);
+        cudaFuncSetAttribute(k_expand_alt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStageBytes);
+        cudaFuncSetAttribute(k_run, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStageBytes);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_expand, kThreads, kStageBytes);
         ls.level_blocks = sms * std::max(per, 1);
         per = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_run, kThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_run, kThreads, kStageBytes);
         ls.run_blocks = sms * std::max(per, 1);
         done = true;
     }
@@ -1848,8 +1927,8 @@ int launch_level(const Eng& E, cudaStream_t st, int blocks, cudaStream_t side = 
         k_sweep<<<blocks, kThreads, 0, st>>>(E);
     }
     if (ex0) FBPT_CUDA_TRY(cudaEventRecord(ex0, st));
-    k_expand<<<blocks, kThreads, 0, st>>>(E);
-    if (E.alt) k_expand_alt<<<blocks, kThreads, 0, st>>>(E);
+    k_expand<<<blocks, kThreads, kStageBytes, st>>>(E);
+    if (E.alt) k_expand_alt<<<blocks, kThreads, kStageBytes, st>>>(E);
     if (ex1) FBPT_CUDA_TRY(cudaEventRecord(ex1, st));
     if (side) FBPT_CUDA_TRY(cudaStreamWaitEvent(st, join, 0));
     k_commit<<<blocks, kThreads, 0, st>>>(E);
@@ -1868,7 +1947,8 @@ int run_persistent(const Eng& E, cudaStream_t st) {
     const LaunchShape ls = launch_shape();
     Eng e = E;
     void* args[] = {(void*)&e};
-    cudaError_t err = cudaLaunchCooperativeKernel((const void*)k_run, dim3(ls.run_blocks), dim3(kThreads), args, 0, st);
+    cudaError_t err =
+        cudaLaunchCooperativeKernel((const void*)k_run, dim3(ls.run_blocks), dim3(kThreads), args, kStageBytes, st);
     if (err != cudaSuccess) {
         cudaGetLastError();
         return fail(FBPT_ECUDA, std::string("cooperative launch: ") + cudaGetErrorString(err));

@@ -260,9 +260,16 @@ extern "C" int fbpt_select_seeds_noalloc(const fbpt_rrsets* rr, uint32_t k, uint
         k_cover_rows<<<cblocks, 256, 0, st>>>(best, r, n, rr->offsets, rr->verts, S, covered, gain, selected, seeds,
                                               gains);
     }
-    FBPT_CUDA_TRY(cudaGetLastError());
-    FBPT_CUDA_TRY(cudaMemcpyAsync(seeds_host, seeds, sizeof(uint32_t) * k, cudaMemcpyDeviceToHost, st));
-    if (gains_host) FBPT_CUDA_TRY(cudaMemcpyAsync(gains_host, gains, sizeof(uint64_t) * k, cudaMemcpyDeviceToHost, st));
-    FBPT_CUDA_TRY(cudaStreamSynchronize(st));
+    // from here on, work that uses the shared array is queued: on any error, wait
+    // for it before returning so that a following call cannot overlap it
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(seeds_host, seeds, sizeof(uint32_t) * k, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && gains_host)
+        e = cudaMemcpyAsync(gains_host, gains, sizeof(uint64_t) * k, cudaMemcpyDeviceToHost, st);
+    const cudaError_t es = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = es;
+    if (e != cudaSuccess)
+        return fail(FBPT_ECUDA, std::string("fbpt_select_seeds_noalloc: ") + cudaGetErrorString(e));
     return FBPT_OK;
 }

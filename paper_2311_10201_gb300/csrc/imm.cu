@@ -2,8 +2,11 @@
 // sampler that Section 2 describes: estimate a lower bound LB on the optimum
 // influence from growing samples, fix theta = ceil(lambda* / LB) RR sets, run
 // greedy max-k-cover over them.  The loop is host logic; every sampling step is
-// sample_impl and every selection fbpt_select_seeds.  The sample grows by
-// appending the RR sets of the next sample ids, never redrawing earlier ones.
+// sample_impl and every selection fbpt_select_seeds.  The estimation sample
+// grows by appending the RR sets of the next sample ids, never redrawing
+// earlier ones; the final selection runs over theta RR sets drawn afresh, with
+// the sample ids after the estimation's (Chen 2018: reusing the estimation sets
+// breaks the martingale argument behind IMM's guarantee).
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -47,19 +50,24 @@ int rr_append(fbpt_rrsets* acc, fbpt_rrsets* add) {
     if (cudaMallocAsync(&verts, sizeof(uint32_t) * std::max<uint64_t>(total, 1), st) != cudaSuccess)
         return undo("vertices");
     if (cudaMallocAsync(&starts, sizeof(uint32_t) * S, st) != cudaSuccess) return undo("starts");
-    FBPT_CUDA_TRY(cudaMemcpyAsync(off, acc->offsets, sizeof(uint64_t) * acc->S, cudaMemcpyDeviceToDevice, st));
     const int blocks = device_sm_count() * 4;
-    k_shift_offsets<<<blocks, 256, 0, st>>>(add->offsets, add->S + 1, acc->total, off + acc->S);
-    if (acc->total)
-        FBPT_CUDA_TRY(cudaMemcpyAsync(verts, acc->verts, sizeof(uint32_t) * acc->total, cudaMemcpyDeviceToDevice, st));
-    if (add->total)
-        FBPT_CUDA_TRY(cudaMemcpyAsync(verts + acc->total, add->verts, sizeof(uint32_t) * add->total,
-                                      cudaMemcpyDeviceToDevice, st));
-    FBPT_CUDA_TRY(cudaMemcpyAsync(starts, acc->starts, sizeof(uint32_t) * acc->S, cudaMemcpyDeviceToDevice, st));
-    FBPT_CUDA_TRY(cudaMemcpyAsync(starts + acc->S, add->starts, sizeof(uint32_t) * add->S, cudaMemcpyDeviceToDevice,
-                                  st));
-    k_add_counts<<<blocks, 256, 0, st>>>(acc->vcount, add->vcount, acc->n);
-    FBPT_CUDA_TRY(cudaGetLastError());
+    bool ok = cudaMemcpyAsync(off, acc->offsets, sizeof(uint64_t) * acc->S, cudaMemcpyDeviceToDevice, st) == cudaSuccess;
+    if (ok) k_shift_offsets<<<blocks, 256, 0, st>>>(add->offsets, add->S + 1, acc->total, off + acc->S);
+    if (ok && acc->total)
+        ok = cudaMemcpyAsync(verts, acc->verts, sizeof(uint32_t) * acc->total, cudaMemcpyDeviceToDevice, st) ==
+             cudaSuccess;
+    if (ok && add->total)
+        ok = cudaMemcpyAsync(verts + acc->total, add->verts, sizeof(uint32_t) * add->total, cudaMemcpyDeviceToDevice,
+                             st) == cudaSuccess;
+    if (ok) ok = cudaMemcpyAsync(starts, acc->starts, sizeof(uint32_t) * acc->S, cudaMemcpyDeviceToDevice, st) ==
+                 cudaSuccess;
+    if (ok) ok = cudaMemcpyAsync(starts + acc->S, add->starts, sizeof(uint32_t) * add->S, cudaMemcpyDeviceToDevice,
+                                 st) == cudaSuccess;
+    if (ok) k_add_counts<<<blocks, 256, 0, st>>>(acc->vcount, add->vcount, acc->n);
+    if (!ok || cudaGetLastError() != cudaSuccess) {
+        cudaStreamSynchronize(st);  // nothing queued may still touch the buffers freed below
+        return undo("device copies");
+    }
     cudaFreeAsync(acc->offsets, st);
     cudaFreeAsync(acc->verts, st);
     cudaFreeAsync(acc->starts, st);
@@ -144,8 +152,18 @@ int imm_impl(fbpt_graph* g, uint32_t k, double epsilon, double ell, uint64_t see
         }
     }
     const uint64_t theta = (uint64_t)std::ceil(lam_s / LB);
-    if (rc == FBPT_OK) rc = extend(theta);
-    if (rc == FBPT_OK) rc = fbpt_select_seeds(&R, k, seeds.data(), gains.data());
+    const uint64_t first_final = have;
+    fbpt_rrsets Fin;
+    std::memset(&Fin, 0, sizeof(Fin));
+    if (rc == FBPT_OK && max_samples && theta > max_samples)
+        rc = fail(FBPT_EINVAL, "fbpt_imm: the final sample needs " + std::to_string(theta) +
+                                   " RR sets, above max_samples");
+    fbpt_rrsets_free(&R);
+    if (rc == FBPT_OK) rc = sample_impl(g, seed, first_final, theta, opts, &Fin, stats);
+    if (rc == FBPT_OK) {
+        have = theta;
+        rc = fbpt_select_seeds(&Fin, k, seeds.data(), gains.data());
+    }
     if (rc == FBPT_OK) {
         if (seeds_host) std::memcpy(seeds_host, seeds.data(), sizeof(uint32_t) * k);
         if (gains_host) std::memcpy(gains_host, gains.data(), sizeof(uint64_t) * k);
@@ -158,9 +176,10 @@ int imm_impl(fbpt_graph* g, uint32_t k, double epsilon, double ell, uint64_t see
             result->lambda_prime = lam_p;
             result->lambda_star = lam_s;
             result->rounds = rounds;
+            result->first_final_id = first_final;
         }
     }
-    fbpt_rrsets_free(&R);
+    fbpt_rrsets_free(&Fin);
     return rc;
 }
 

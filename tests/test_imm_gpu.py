@@ -27,7 +27,8 @@ def check(fbpt, g, k, eps, ell, seed, **kw):
     seeds, gains, res, st = fbpt.imm(dg, k, eps, ell, seed, **kw)
     rs, rg, info = oimm.imm(g, k, eps, ell, seed)
     assert np.array_equal(seeds, rs) and np.array_equal(gains, rg)
-    for key in ("theta", "samples", "rounds", "lower_bound", "coverage", "lambda_prime", "lambda_star"):
+    for key in ("theta", "samples", "first_final_id", "rounds", "lower_bound", "coverage", "lambda_prime",
+                "lambda_star"):
         assert res[key] == info[key], key
     dg.close()
     return res, st

@@ -62,7 +62,9 @@ def test_star_rounds_and_theta_by_hand():
     assert info["rounds"] == 1
     assert info["lower_bound"] == n / (1.0 + epsp)
     assert info["theta"] == math.ceil(lam_s / (n / (1.0 + epsp)))
-    assert info["samples"] == max(info["theta"], math.ceil(lam_p / (n / 2.0)))
+    # the final selection runs over theta fresh sets, after the round's lambda' / (n / 2)
+    assert info["samples"] == info["theta"]
+    assert info["first_final_id"] == math.ceil(lam_p / (n / 2.0))
     assert seeds.tolist() == [0] and gains.tolist() == [info["samples"]]
     assert info["coverage"] == 1.0
 
