@@ -30,10 +30,13 @@ import synth  # noqa: E402
 
 WORKLOAD = "rmat_s22_wc"
 # DRAM bytes (read + write) per 4-edge group of a k_expand launch, from an ncu
-# capture of the current kernel; the bench scales it by its own groups per
-# launch.  None when the kernel has changed since the last capture.
-EXPAND_DRAM_BYTES_PER_GROUP = None
-EXPAND_TRAFFIC_NOTE = "no capture of the current expand kernel yet"
+# capture of the current kernel on the s22 workload (five launches, levels
+# 600-604: 683,459,072 B over 19,737,581 groups); the bench scales it by its
+# own groups per launch.  None when the kernel has changed since the capture.
+EXPAND_DRAM_BYTES_PER_GROUP = (135972864 + 136235776 + 135722240 + 135628288 + 134960640 +
+                               3196928 + 768768 + 338688 + 308224 + 333568) / 19737581
+EXPAND_TRAFFIC_NOTE = ("ncu dram__bytes_read + dram__bytes_write per group of the current kernel "
+                       "(s22 levels 600-604) x this run's groups per launch")
 METRIC = "RR samples/s (bit-exact RR sets + greedy seeds, R-MAT s22 WC, 1,048,576 samples, k=100)"
 
 
@@ -315,9 +318,10 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-fused comparison on this workload")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffers) measurement")
-    ap.add_argument("--order", default="identity", choices=["identity", "rcm", "degree", "random", "cluster"],
+    ap.add_argument("--order", default="degree", choices=["identity", "rcm", "degree", "random", "cluster"],
                     help="vertex order of the sampled graph (host preprocessing, outside the timed steps)")
-    ap.add_argument("--sorted-starts", action="store_true", help="samples take lanes by start vertex")
+    ap.add_argument("--sorted-starts", action=argparse.BooleanOptionalAction, default=True,
+                    help="samples take lanes by (relabelled) start vertex")
     ap.add_argument("--fused-steps", type=int, default=2,
                     help="timed calls per arm of the fused-vs-unfused W sweep on R-MAT s20 (0 = skip)")
     ap.add_argument("--s24-samples", type=int, default=65536,
@@ -358,8 +362,11 @@ def main():
     stream = torch.cuda.current_stream()
     dg = fbpt.Graph.from_synth(g, stream)
     perm = None
+    order_s = 0.0
     if args.order != "identity" or args.sorted_starts:
+        t0 = time.perf_counter()
         perm = fbpt.order_compute(g.n, g.row_ptr, g.col, args.order)
+        order_s = time.perf_counter() - t0
         dg.set_order(perm, args.sorted_starts)
     # launch shape: measured by the autotuner before the timed region (like a
     # library's algorithm search), unless given on the command line
@@ -443,17 +450,20 @@ def main():
                "theta": ires["theta"], "rounds": ires["rounds"], "lower_bound": ires["lower_bound"],
                "coverage": ires["coverage"], "samples_per_s": ires["samples"] / dt}
 
-    # ---- the same step on a relabelled graph (Section 5: vertices by
-    # decreasing degree, samples taking lanes by start vertex); the order is
-    # host preprocessing like the graph upload, outside the timed steps, and
-    # the RR sets are the same bits ----
+    # ---- the same step in the other vertex order (Section 5: vertices
+    # relabelled by decreasing degree, samples taking lanes by start vertex,
+    # against the caller's order): the order is host preprocessing like the
+    # graph upload, outside the timed steps, and the RR sets are the same bits ----
     ordered = None
-    if rank == 0 and world == 1 and not args.no_plain and perm is None:
+    if rank == 0 and world == 1 and not args.no_plain:
         try:
             t0 = time.perf_counter()
-            perm = fbpt.order_compute(g.n, g.row_ptr, g.col, "degree")
+            if perm is None:
+                operm, o_name, o_sorted = fbpt.order_compute(g.n, g.row_ptr, g.col, "degree"), "degree", True
+            else:
+                operm, o_name, o_sorted = None, "identity", False
             host_s = time.perf_counter() - t0
-            dg.set_order(perm, True)
+            dg.set_order(operm, o_sorted)
             warm, _ = step()
             ref_total = warm.total
             del warm
@@ -469,15 +479,16 @@ def main():
             e1.record(stream)
             torch.cuda.synchronize()
             oms = e0.elapsed_time(e1) / osteps
-            ordered = {"order": "degree", "sorted_starts": True, "value": S / (oms / 1e3), "unit": "RR samples/s",
+            ordered = {"order": o_name, "sorted_starts": o_sorted, "value": S / (oms / 1e3), "unit": "RR samples/s",
                        "ms_per_step": oms, "steps": osteps, "host_order_s": host_s, "levels": int(ost.levels),
                        "groups_expanded": int(ost.groups_expanded), "rr_total": int(ref_total),
-                       "same_rr_total": int(ref_total) == int(st.rr_total)}
+                       "same_rr_total": int(ref_total) == int(st.rr_total),
+                       "headline_over_this": (S / (ms_step / 1e3)) / (S / (oms / 1e3))}
         except Exception as ex:  # reported, never fatal to the line
             ordered = {"error": str(ex)[:200]}
         finally:
             try:
-                dg.set_order(None, False)
+                dg.set_order(perm, args.sorted_starts if perm is not None else False)
             except Exception:
                 pass
 
@@ -609,6 +620,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": args.workload, "graph": g.name, "n": g.n, "m": g.m, "samples_per_gpu": S, "k": k,
                        "shape": kw, "autotuned": tuned, "order": args.order, "sorted_starts": args.sorted_starts,
+                       "host_order_s": order_s,
                        "l2": "inputs larger than L2 (in-CSR + thresholds %.0f MB)" % ((g.m * 8 + g.n * 8) / 1e6)},
             "plain_fused": plain, "ordered": ordered, "lt": lt, "batched_32": batched, "imm": imm,
             "fused_vs_unfused_s20": fused, "s24_tri": s24,

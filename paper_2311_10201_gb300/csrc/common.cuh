@@ -155,6 +155,21 @@ __device__ __forceinline__ T warp_alloc(T* ctr, T count) {
     return base + incl - count;
 }
 
+// Two warp-aggregated allocations at once: lane 31 bumps both counters before
+// either result is awaited.  All 32 lanes must call.
+template <typename T>
+__device__ __forceinline__ void warp_alloc2(T* ca, T na, T& ra, T* cb, T nb, T& rb) {
+    const T ia = warp_incl_scan(na), ib = warp_incl_scan(nb);
+    const T ta = __shfl_sync(0xffffffffu, ia, 31), tb = __shfl_sync(0xffffffffu, ib, 31);
+    T ba = 0, bb = 0;
+    if (lane_id() == 31) {
+        if (ta) ba = atomicAdd(ca, ta);
+        if (tb) bb = atomicAdd(cb, tb);
+    }
+    ra = __shfl_sync(0xffffffffu, ba, 31) + ia - na;
+    rb = __shfl_sync(0xffffffffu, bb, 31) + ib - nb;
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll

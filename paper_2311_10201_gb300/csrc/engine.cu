@@ -1064,20 +1064,21 @@ __device__ void dev_commit(const Eng& E, Smem& sm) {
         }
         mwords += units ? (E.unfused ? units : (uint64_t)__popcll(occ)) : 0;
         ncol += units ? bits : 0;
+        // narrow units: (units | groups << 26); wide: a record and chunks of
+        // their own per unit (64-group blocks times colour blocks; one colour
+        // per unfused unit), (units | chunks << 26).  Both counters are bumped
+        // by one lane before either result is awaited.
         const unsigned long long req = (unsigned long long)((nun * ng) << kUnitBits) | nun;
-        const unsigned long long got = warp_alloc<unsigned long long>(&ctl->new_packed, req);
+        const uint64_t wun = wide ? units : 0;
+        const uint64_t ncb = E.unfused ? 1 : (bits + kColourBlock - 1) / kColourBlock;
+        const uint64_t wck = wide ? ((ng + kWideSpan - 1) / kWideSpan) * ncb : 0;
+        const unsigned long long wreq = (unsigned long long)((wun * wck) << kUnitBits) | wun;
+        unsigned long long got, wgot;
+        warp_alloc2<unsigned long long>(&ctl->new_packed, req, got, &ctl->wide_packed, wreq, wgot);
         const uint64_t pos0 = got & kUnitMask;
         const uint64_t gbeg0 = got >> kUnitBits;
         const bool fits = nun && pos0 + nun <= E.list_cap;
         if (nun && !fits) atomicOr(&ctl->error, (unsigned)kErrListOverflow);
-        // wide: a record and ceil(ng / 32) chunks of its own per unit
-        const uint64_t wun = wide ? units : 0;
-        // chunks of a wide unit: 32-group blocks times colour blocks (one
-        // colour per unfused unit)
-        const uint64_t ncb = E.unfused ? 1 : (bits + kColourBlock - 1) / kColourBlock;
-        const uint64_t wck = wide ? ((ng + kWideSpan - 1) / kWideSpan) * ncb : 0;
-        const unsigned long long wgot =
-            warp_alloc<unsigned long long>(&ctl->wide_packed, (unsigned long long)((wun * wck) << kUnitBits) | wun);
         const uint64_t wpos = wgot & kUnitMask, wc0 = wgot >> kUnitBits;
         const bool wfits = wide && wpos + wun <= E.list_cap && wc0 + wun * wck <= E.wide_chunk_cap;
         if (wide && !wfits) {
