@@ -33,10 +33,8 @@ WORKLOAD = "rmat_s22_wc"
 # capture of the current kernel on the s22 workload (five launches, levels
 # 600-604: 683,459,072 B over 19,737,581 groups); the bench scales it by its
 # own groups per launch.  None when the kernel has changed since the capture.
-EXPAND_DRAM_BYTES_PER_GROUP = (135972864 + 136235776 + 135722240 + 135628288 + 134960640 +
-                               3196928 + 768768 + 338688 + 308224 + 333568) / 19737581
-EXPAND_TRAFFIC_NOTE = ("ncu dram__bytes_read + dram__bytes_write per group of the current kernel "
-                       "(s22 levels 600-604) x this run's groups per launch")
+EXPAND_DRAM_BYTES_PER_GROUP = None
+EXPAND_TRAFFIC_NOTE = "no ncu capture of the current kernel"
 METRIC = "RR samples/s (bit-exact RR sets + greedy seeds, R-MAT s22 WC, 1,048,576 samples, k=100)"
 
 
@@ -536,23 +534,30 @@ def main():
         except Exception as ex:  # reported, never fatal to the line
             s24 = {"error": str(ex)[:200]}
 
-    # ---- roofline of the dominant kernel (the push expand), per launch ----
-    # HBM is the roofline: nothing on the path is a dense contraction.
-    # Algorithmic bytes of one launch: 8 B of col + thr per in-edge read (edge
-    # accesses), 40 B per frontier unit (its record and chunk-map entry), 8 B per
-    # colour word of a unit (stage word).  The launch duration is measured with
-    # CUDA events around every expand launch of one host-launched call of the
-    # same shape right after the timed steps (inside the timed graph launch all
-    # levels run within one launch); the device %globaltimer brackets of the
-    # expand in the timed steps are reported beside it.  Secondary view: the
-    # liveness draws against the measured rate of a Philox-only kernel.
-    launches = max(int(st.push_levels), 1)
-    alg_bytes = (8 * st.edge_accesses + 40 * st.units_expanded + 8 * st.mask_words) / launches
+    # ---- roofline of the dominant kernel (the level's first kernel), per launch ----
+    # HBM is the roofline: nothing on the path is a dense contraction.  The
+    # kernel places the new start vertices, expands the frontier and sweeps the
+    # finished lanes.  Algorithmic bytes of one launch: expand, 8 B of col + thr
+    # per in-edge read (edge accesses), 40 B per frontier unit (its record and
+    # chunk-map entry), 8 B per colour word of a unit (stage word); init, 40 B per
+    # started sample (start id, next and occupancy words read and written, a
+    # pending entry); sweep, 32 B per RR entry (segment entry read, staging
+    # entry written, visited word and vertex count read and written; 36 B with
+    # a vertex order, whose inverse is read).  The launch duration is measured
+    # with CUDA events around every expand launch of one host-launched call of
+    # the same shape right after the timed steps (inside the timed graph launch
+    # all levels run within one launch); the device %globaltimer brackets of the
+    # expand phase in the timed steps are reported beside it.  Secondary view:
+    # the liveness draws against the measured rate of a Philox-only kernel.
+    launches = max(int(st.levels), 1)
+    sweep_b = 36 if perm is not None else 32
+    alg_bytes = (8 * st.edge_accesses + 40 * st.units_expanded + 8 * st.mask_words + 40 * S
+                 + sweep_b * st.rr_total) / launches
     pk, pk_kind = peaks()
     ev_rr = fbpt.sample(dg, seed, first, S, **dict(kw, launch="host"))
     ev = ev_rr.stats
     del ev_rr
-    ev_launches = max(int(ev.push_levels), 1)
+    ev_launches = max(int(ev.levels), 1)
     launch_s = ev.ms_expand_events * 1e-3 / ev_launches
     achieved = alg_bytes / launch_s / 1e9 if launch_s > 0 else 0.0
     exp_s = st.ms_expand * 1e-3

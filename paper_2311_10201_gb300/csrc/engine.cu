@@ -21,11 +21,12 @@
 //   commit   pending vertices -> visited, new frontier list, lane entry lists
 //   schedule (one CTA) finished lanes, refills, loop condition
 //   init     start vertices of lanes assigned a new sample
-// They run as four kernels per level (host loop or CUDA-graph WHILE loop, where
-// the sweep is a branch beside the expand; the scheduler CTA also places the
-// start vertices) or inside one persistent cooperative kernel, where sweep,
-// init and expand of a level share a phase and bounded grid barriers separate
-// the phases.
+// They run as three kernels per level (host loop or CUDA-graph WHILE loop):
+// init, expand and sweep in one kernel (init first, the sweep in its tail), the
+// commit, and the scheduler CTA; a level that expands by filtered push or pull
+// adds a second expand kernel.  Or inside one persistent cooperative kernel,
+// where sweep, init and expand of a level share a phase and bounded grid
+// barriers separate the phases.
 //
 // Liveness never reads visited[]: the expand draws for every colour of the
 // frontier mask and the commit removes colours a vertex has already seen.
@@ -251,8 +252,8 @@ __device__ void dev_sweep(const Eng& E, uint32_t* pre, uint64_t* fin) {
 }
 
 // ---- init: start vertices of lanes given a new sample (Listing 1's frontier initialization) ------
-// The persistent kernel runs this over all its CTAs; in the per-level forms the
-// scheduler CTA places the start vertices itself (dev_schedule<.., true>).
+// Runs over all CTAs of the level's first kernel (the persistent kernel, or the
+// per-level expand) from the lanes the last schedule marked in init_w.
 
 __device__ void dev_init(const Eng& E) {
     Ctl* ctl = E.ctl;
@@ -1348,9 +1349,9 @@ __device__ __forceinline__ void block_scan_multi(unsigned long long (&v)[kScanVa
 // frontier list becomes the expand's input; the loop continues while any
 // lane holds a sample.  Every thread owns a run of consecutive lanes (inside
 // one word; at most kPer of them), so lane-order prefixes are block scans.
-// With init, the CTA also places the start vertex of every lane given a
-// sample (one lane per thread); otherwise dev_init does it from init_w.
-template <uint32_t kPer, bool init>
+// The start vertices of the lanes given a sample are placed by the next
+// level's first kernel (dev_init, from init_w).
+template <uint32_t kPer>
 __device__ void dev_schedule(const Eng& E, Smem& sm) {
     Ctl* ctl = E.ctl;
     const uint32_t t = threadIdx.x;
@@ -1467,7 +1468,6 @@ __device__ void dev_schedule(const Eng& E, Smem& sm) {
             if ((freem >> c) & 1ull) {
                 if (r < avail) {
                     ctl->lane_j[a0 + c] = E.order ? __ldg(&E.order[h.next_j + r]) : (uint32_t)(h.next_j + r);
-                    if (init) sm.lane[r] = a0 + c;  // r < L: the new lanes in lane order
                     got |= 1ull << c;
                 }
                 ++r;
@@ -1477,55 +1477,10 @@ __device__ void dev_schedule(const Eng& E, Smem& sm) {
     }
     __syncthreads();
     if (t < WB) {
-        ctl->init_w[t] = init ? 0ull : sm.init[t];
+        ctl->init_w[t] = sm.init[t];
         ctl->run_w[t] = sm.still[t] | sm.init[t];
         ctl->still_w[t] = sm.still[t];
         ctl->act_w[t] = 0;
-    }
-    // the start vertices of the new lanes (Listing 1's frontier initialization).
-    // The commit has cleared next[] and nocc[] of every row it took, so both are
-    // zero here: a lane sets its bits with two independent atomics, the lane
-    // that first marks nocc[v] lists v as pending, and the pending list (which
-    // the commit has consumed) restarts with these vertices at block-scan
-    // positions.
-    if (init) {
-        const uint32_t lane = lane_id(), warp = t >> 5, nw = blockDim.x >> 5;
-        uint32_t listed = 0;
-        for (uint32_t base = 0; base < (uint32_t)assigned; base += blockDim.x) {
-            const uint32_t r = base + t;
-            uint32_t v = 0;
-            bool first = false;
-            if (r < (uint32_t)assigned) {
-                const uint32_t l = sm.lane[r];
-                const uint64_t j = E.order ? (uint64_t)__ldg(&E.order[h.next_j + r]) : h.next_j + r;
-                const uint32_t v0 = start_vertex(E.seed, E.first_id + j, E.n);
-                E.starts[j] = v0;
-                v = E.perm ? __ldg(&E.perm[v0]) : v0;
-                const uint32_t i = l >> 6;
-                atomicOr((unsigned long long*)&E.next[(uint64_t)v * E.WB + i], 1ull << (l & 63));
-                first = atomicOr((unsigned long long*)&E.nocc[v], 1ull << i) == 0ull;
-            }
-            const unsigned bal = __ballot_sync(0xffffffffu, first);
-            if (lane == 0) sm.mscan[warp][0] = __popc(bal);
-            __syncthreads();
-            if (warp == 0) {
-                const unsigned long long x = lane < nw ? sm.mscan[lane][0] : 0ull;
-                const unsigned long long xi = warp_incl_scan(x);
-                if (lane < nw) sm.mscan[lane][0] = xi - x;
-                if (lane == 31) sm.mscan[32][0] = xi;
-            }
-            __syncthreads();
-            if (first) {
-                const uint64_t p = listed + sm.mscan[warp][0] + __popc(bal & lanemask_lt());
-                if (p < E.pend_cap)
-                    E.pend_v[p] = v;
-                else
-                    atomicOr(&ctl->error, (unsigned)kErrPendOverflow);
-            }
-            listed += (uint32_t)sm.mscan[32][0];
-            __syncthreads();
-        }
-        if (t == 0) ctl->pend_count = listed;
     }
     const bool any_run = nstill != 0 || assigned != 0;
     // 5. direction of the coming level
@@ -1637,7 +1592,7 @@ __device__ void dev_schedule(const Eng& E, Smem& sm) {
         }
         ctl->new_packed = 0;
         ctl->chunk_next = 0;
-        if (!init) ctl->pend_count = 0;
+        ctl->pend_count = 0;
         ctl->tick = tick + 1;
         uint32_t run = any_run ? 1u : 0u;
         if (tick + 1 > h.tick_limit) {
@@ -1659,11 +1614,19 @@ __global__ void __launch_bounds__(kThreads) k_sweep(const Eng E) {
     __shared__ uint64_t fin[kMaxWords];
     dev_sweep(E, pre, fin);
 }
+// The level's first kernel: the start vertices of the lanes the last schedule
+// refilled, the push expand, then this CTA's share of the sweep of the lanes
+// that finished at the last level (its shared memory reused), so that the sweep
+// runs in the expand's tail without a launch of its own.
 __global__ void __launch_bounds__(kThreads, FBPT_EXPAND_MINB) k_expand(const Eng E) {
-    __shared__ uint32_t lane_j[kMaxLanes];
+    __shared__ uint32_t lane_j[kMaxLanes + 1];
     __shared__ uint32_t pcnt[kThreads / 32], pbuf[kThreads / 32 * kPendBuf];
+    __shared__ uint64_t fin[kMaxWords];
     extern __shared__ uint4 pstage[];  // kStageBytes, dynamic
+    dev_init(E);
     dev_expand<kPartPush>(E, lane_j, pcnt, pbuf, pstage);
+    __syncthreads();
+    dev_sweep(E, lane_j, fin);
 }
 __global__ void __launch_bounds__(kThreads) k_expand_alt(const Eng E) {
     __shared__ uint32_t lane_j[kMaxLanes];
@@ -1677,7 +1640,7 @@ __global__ void __launch_bounds__(kThreads) k_commit(const Eng E) {
 }
 __global__ void __launch_bounds__(kSchedThreads) k_schedule(const Eng E) {
     __shared__ Smem sm;
-    dev_schedule<kMaxLanes / kSchedThreads, true>(E, sm);
+    dev_schedule<kMaxLanes / kSchedThreads>(E, sm);
 }
 
 // ---- persistent form: the whole run in one cooperative launch -------------------------------
@@ -1703,7 +1666,7 @@ __device__ bool grid_barrier(const Eng& E, Smem& sm, unsigned& gen, bool schedul
     __syncthreads();
     if (sm.last) {
         __threadfence();
-        if (schedule) dev_schedule<kMaxLanes / kThreads, false>(E, sm);
+        if (schedule) dev_schedule<kMaxLanes / kThreads>(E, sm);
         if (threadIdx.x == 0) {
             ctl->bar_count = 0;
             __threadfence();
@@ -1911,27 +1874,19 @@ int order_rows(const uint32_t* rows_v, const uint64_t* row_start, const uint32_t
     return FBPT_OK;
 }
 
-// One level.  With a side stream (graph capture), the sweep runs on it beside
-// the expand: the sweep touches the finished lanes' segments, the spill log,
+// One level: expand (with the start vertices and the sweep of the last level's
+// finished lanes), the filtered/pull expand when the level takes it, commit and
+// schedule.  The sweep touches the finished lanes' segments, the spill log,
 // visited[], the RR staging rows and the counts; the expand reads the frontier
 // list, col/thr and the lanes' sample ids and writes next[], nocc[] and the
-// pending list, so the two may overlap; the commit waits for both.
-int launch_level(const Eng& E, cudaStream_t st, int blocks, cudaStream_t side = nullptr,
-                 cudaEvent_t fork = nullptr, cudaEvent_t join = nullptr, cudaEvent_t ex0 = nullptr,
-                 cudaEvent_t ex1 = nullptr) {
-    if (side) {
-        FBPT_CUDA_TRY(cudaEventRecord(fork, st));
-        FBPT_CUDA_TRY(cudaStreamWaitEvent(side, fork, 0));
-        k_sweep<<<blocks, kThreads, 0, side>>>(E);
-        FBPT_CUDA_TRY(cudaEventRecord(join, side));
-    } else {
-        k_sweep<<<blocks, kThreads, 0, st>>>(E);
-    }
+// pending list, so the two may share the kernel in any order across its CTAs;
+// the commit, which reads visited[], follows the whole kernel.  ex0/ex1 bracket
+// the expand launches.
+int launch_level(const Eng& E, cudaStream_t st, int blocks, cudaEvent_t ex0 = nullptr, cudaEvent_t ex1 = nullptr) {
     if (ex0) FBPT_CUDA_TRY(cudaEventRecord(ex0, st));
     k_expand<<<blocks, kThreads, kStageBytes, st>>>(E);
     if (E.alt) k_expand_alt<<<blocks, kThreads, kStageBytes, st>>>(E);
     if (ex1) FBPT_CUDA_TRY(cudaEventRecord(ex1, st));
-    if (side) FBPT_CUDA_TRY(cudaStreamWaitEvent(st, join, 0));
     k_commit<<<blocks, kThreads, 0, st>>>(E);
     k_schedule<<<1, kSchedThreads, 0, st>>>(E);
     FBPT_CUDA_TRY(cudaGetLastError());
@@ -1972,28 +1927,20 @@ int add_level_loop(cudaGraph_t graph, const cudaGraphNode_t* deps, size_t ndeps,
     if (cudaGraphAddNode(node, graph, deps, nullptr, ndeps, &p) != cudaSuccess)
         return fail(FBPT_ECUDA, "cudaGraphAddNode(conditional) failed");
     cudaGraph_t body = p.conditional.phGraph_out[0];
-    cudaStream_t cs = nullptr, side = nullptr;
-    cudaEvent_t fork = nullptr, join = nullptr;
+    cudaStream_t cs = nullptr;
     auto release = [&]() {
-        if (fork) cudaEventDestroy(fork);
-        if (join) cudaEventDestroy(join);
-        if (side) cudaStreamDestroy(side);
         if (cs) cudaStreamDestroy(cs);
     };
-    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&join, cudaEventDisableTiming) != cudaSuccess) {
-        release();
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
         cudaGetLastError();
-        return fail(FBPT_ECUDA, "stream or event create failed");
+        return fail(FBPT_ECUDA, "stream create failed");
     }
     E.cond = (unsigned long long)h;
     if (cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
         release();
         return fail(FBPT_ECUDA, "cudaStreamBeginCaptureToGraph failed");
     }
-    const int lrc = launch_level(E, cs, blocks, side, fork, join);
+    const int lrc = launch_level(E, cs, blocks);
     cudaGraph_t captured = nullptr;
     const cudaError_t ce = cudaStreamEndCapture(cs, &captured);
     release();
@@ -2381,7 +2328,7 @@ int run_enqueue(Run& r) {
         }
         r.expand_event_ms = 0.0;
         for (;;) {
-            rc = launch_level(r.E, st, r.blocks, nullptr, nullptr, nullptr, ex0, ex1);
+            rc = launch_level(r.E, st, r.blocks, ex0, ex1);
             if (rc != FBPT_OK) break;
             if (cudaMemcpyAsync(&r.H->running, &ws->ctl->running, sizeof(unsigned), cudaMemcpyDeviceToHost, st) !=
                     cudaSuccess ||
