@@ -29,12 +29,15 @@ sys.path.insert(0, ROOT)
 import synth  # noqa: E402
 
 WORKLOAD = "rmat_s22_wc"
-# DRAM bytes (read + write) per 4-edge group of a k_expand launch, from an ncu
-# capture of the current kernel on the s22 workload (five launches, levels
-# 600-604: 683,459,072 B over 19,737,581 groups); the bench scales it by its
-# own groups per launch.  None when the kernel has changed since the capture.
-EXPAND_DRAM_BYTES_PER_GROUP = None
-EXPAND_TRAFFIC_NOTE = "no ncu capture of the current kernel"
+# DRAM bytes (read + write) per 4-edge group of a k_expand launch (start
+# vertices, expand and sweep), from an ncu capture of the current kernel on the
+# s22 workload in degree order (five launches, levels 600-604: 764,330,752 B over
+# 21,148,211 groups); the bench scales it by its own groups per launch.  None
+# when the kernel has changed since the capture.
+EXPAND_DRAM_BYTES_PER_GROUP = ((151961344 + 151427328 + 152355328 + 151352320 + 151691776) +
+                               (3368704 + 489984 + 512256 + 743936 + 427776)) / 21148211
+EXPAND_TRAFFIC_NOTE = ("ncu dram__bytes_read + dram__bytes_write per group of the current kernel "
+                       "(s22, degree order, levels 600-604) x this run's groups per launch")
 METRIC = "RR samples/s (bit-exact RR sets + greedy seeds, R-MAT s22 WC, 1,048,576 samples, k=100)"
 
 
@@ -614,9 +617,11 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(g, seed, 8192)
 
-    # kernels per step: 4 or 5 per level, the final sweep, the row-length scan (3), the
-    # three row-ordering kernels, greedy 2 per pick + 3
-    per_level = 4 + (1 if kw.get("schedule", "push") != "push" else 0)  # + the filtered/pull expand
+    # kernels per step: 3 or 4 per level (expand with start vertices and sweep,
+    # commit, scheduler; + the filtered/pull expand when the schedule may pick
+    # it), the final sweep, the row-length scan (3), the three row-ordering
+    # kernels, greedy 2 per pick + 3
+    per_level = 3 + (1 if kw.get("schedule", "push") != "push" else 0)
     launches_step = per_level * int(st.levels) + 1 + 3 + 3 + 2 * k + 3
     if rank == 0:
         print(json.dumps({

@@ -110,6 +110,7 @@ struct Smem {
     unsigned long long still[kMaxWords], sfin[kMaxWords], init[kMaxWords];
     unsigned long long mscan[33][6];  // schedule: block-scan scratch (32 warps + totals)
     float rawf[8], feat[8], h1[kPolicyHidden], h2[kPolicyHidden], out[kPolicyOut];
+    float pol[2 * kPolicyIn + kPolicyParams];  // schedule: the network's parameters
     uint32_t last, abort, nstill, dir, mode;
     uint32_t pcnt[kThreads / 32], pbuf[kThreads / 32 * kPendBuf];  // expand: per-warp pending buffers
 };
@@ -1239,13 +1240,16 @@ __device__ void dev_commit(const Eng& E, Smem& sm) {
 // Features of the coming level (also what the trace rows let a trainer rebuild):
 // log2 of 1 + units, groups, colours and frontier lanes, the frontier's share of
 // the edges (log2 of 4 * groups / m) and log2 of colours per unit.
-__device__ __forceinline__ void level_features(float* f, double U, double G, double C, double L, double m) {
-    f[0] = (float)log2(1.0 + U);
-    f[1] = (float)log2(1.0 + G);
-    f[2] = (float)log2(1.0 + C);
-    f[3] = (float)log2(1.0 + L);
-    f[4] = (float)(log2(1.0 + 4.0 * G) - log2(1.0 + m));
-    f[5] = (float)log2(1.0 + C / (U > 1.0 ? U : 1.0));
+// Feature k of a level (FP64 arithmetic, rounded to FP32).
+__device__ __forceinline__ float level_feature(uint32_t k, double U, double G, double C, double L, double m) {
+    switch (k) {
+        case 0: return (float)log2(1.0 + U);
+        case 1: return (float)log2(1.0 + G);
+        case 2: return (float)log2(1.0 + C);
+        case 3: return (float)log2(1.0 + L);
+        case 4: return (float)(log2(1.0 + 4.0 * G) - log2(1.0 + m));
+        default: return (float)log2(1.0 + C / (U > 1.0 ? U : 1.0));
+    }
 }
 
 // The policy's level actions: outputs 0..4 of the network are the predicted
@@ -1274,8 +1278,9 @@ __device__ __forceinline__ uint32_t heuristic_dir(double U, double G, double C, 
 // are the predicted log2 device time of the level under push, filtered push
 // and pull.  P holds the input mean and scale (6 + 6), then W1 (32x6), b1,
 // W2 (32x32), b2, W3 (8x32), b3.  All threads of the CTA call it.
-__device__ void policy_forward(const float* P, Smem& sm) {
+__device__ void policy_forward(Smem& sm) {
     const int t = threadIdx.x;
+    const float* P = sm.pol;
     const float* mu = P;
     const float* sd = P + kPolicyIn;
     const float* W1 = P + 2 * kPolicyIn;
@@ -1404,6 +1409,22 @@ __device__ void dev_schedule(const Eng& E, Smem& sm) {
         cnt[c] = in ? L2(&ctl->lane_cnt[a0 + c]) : 0u;
         jj[c] = in ? L2(&ctl->lane_j[a0 + c]) : 0u;
     }
+    // the schedule network's parameters (learned schedule only) into shared
+    // memory, loaded together with the fields above (blockDim >= kThreads)
+    if (E.policy) {
+        constexpr uint32_t kN = 2 * kPolicyIn + kPolicyParams, kPP = (kN + kThreads - 1) / kThreads;
+        float pv[kPP];
+#pragma unroll
+        for (uint32_t k = 0; k < kPP; ++k) {
+            const uint32_t i = t + k * blockDim.x;
+            pv[k] = i < kN ? __ldg(&E.policy[i]) : 0.f;
+        }
+#pragma unroll
+        for (uint32_t k = 0; k < kPP; ++k) {
+            const uint32_t i = t + k * blockDim.x;
+            if (i < kN) sm.pol[i] = pv[k];
+        }
+    }
     if (t < WB) sm.init[t] = 0;
     if (a0 < a1 && (a0 & 63) == 0) {  // the first thread of each word keeps its masks
         sm.still[wi] = run & act;
@@ -1490,9 +1511,12 @@ __device__ void dev_schedule(const Eng& E, Smem& sm) {
         const double C = (double)h.new_colours;
         const uint32_t sched = h.sched;
         const bool pull_ok = E.frontd != nullptr;
+        // one feature per warp (lane 0 of warps 1..6): FP64 is slow on this
+        // part, and the six logarithms overlap only in different warps
+        if (((sched == FBPT_SCHED_LEARNED && E.policy) || E.trace) && (t & 31u) == 0 && t >= 32 &&
+            t <= 32u * kPolicyIn && t < blockDim.x)
+            sm.rawf[(t >> 5) - 1] = level_feature((t >> 5) - 1, U, G, C, (double)nstill, (double)E.m);
         if (t == 0) {
-            if ((sched == FBPT_SCHED_LEARNED && E.policy) || E.trace)
-                level_features(sm.rawf, U, G, C, (double)nstill, (double)E.m);
             uint32_t d = kDirPush;
             if (sched == FBPT_SCHED_PULL && pull_ok) d = kDirPull;
             else if (sched == FBPT_SCHED_FILTERED) d = kDirFiltered;
@@ -1510,7 +1534,7 @@ __device__ void dev_schedule(const Eng& E, Smem& sm) {
         }
         __syncthreads();
         if (sched == FBPT_SCHED_LEARNED && E.policy) {
-            policy_forward(E.policy, sm);
+            policy_forward(sm);
             if (t == 0) {
                 // actions: push, filtered push, pull (queue compaction), then push
                 // and filtered push with scan compaction; the smallest predicted time
@@ -1615,31 +1639,36 @@ __global__ void __launch_bounds__(kThreads) k_sweep(const Eng E) {
     dev_sweep(E, pre, fin);
 }
 // The level's first kernel: the start vertices of the lanes the last schedule
-// refilled, the push expand, then this CTA's share of the sweep of the lanes
-// that finished at the last level (its shared memory reused), so that the sweep
-// runs in the expand's tail without a launch of its own.
+// refilled, this CTA's share of the sweep of the lanes that finished at the
+// last level (the first CTAs take it, their shared memory reused for the lane
+// table afterwards), then the push expand, whose chunk counter hands the other
+// CTAs more chunks meanwhile.  No launch of its own for either.
 __global__ void __launch_bounds__(kThreads, FBPT_EXPAND_MINB) k_expand(const Eng E) {
     __shared__ uint32_t lane_j[kMaxLanes + 1];
     __shared__ uint32_t pcnt[kThreads / 32], pbuf[kThreads / 32 * kPendBuf];
     __shared__ uint64_t fin[kMaxWords];
     extern __shared__ uint4 pstage[];  // kStageBytes, dynamic
+    if (E.gated && !L2(&E.ctl->running)) return;
     dev_init(E);
-    dev_expand<kPartPush>(E, lane_j, pcnt, pbuf, pstage);
-    __syncthreads();
     dev_sweep(E, lane_j, fin);
+    __syncthreads();
+    dev_expand<kPartPush>(E, lane_j, pcnt, pbuf, pstage);
 }
 __global__ void __launch_bounds__(kThreads) k_expand_alt(const Eng E) {
     __shared__ uint32_t lane_j[kMaxLanes];
     __shared__ uint32_t pcnt[kThreads / 32], pbuf[kThreads / 32 * kPendBuf];
     extern __shared__ uint4 pstage[];  // kStageBytes, dynamic
+    if (E.gated && !L2(&E.ctl->running)) return;
     dev_expand<kPartAlt>(E, lane_j, pcnt, pbuf, pstage);
 }
 __global__ void __launch_bounds__(kThreads) k_commit(const Eng E) {
     __shared__ Smem sm;
+    if (E.gated && !L2(&E.ctl->running)) return;
     dev_commit(E, sm);
 }
 __global__ void __launch_bounds__(kSchedThreads) k_schedule(const Eng E) {
     __shared__ Smem sm;
+    if (E.gated && !L2(&E.ctl->running)) return;
     dev_schedule<kMaxLanes / kSchedThreads>(E, sm);
 }
 
@@ -2253,6 +2282,7 @@ int run_arm(Run& r) {
     H->dir = r.o.schedule == FBPT_SCHED_FILTERED ? kDirFiltered : kDirPush;
     H->mode = FBPT_COMPACT_QUEUE;  // the first levels carry only the start vertices
     H->refill = r.o.refill == FBPT_REFILL_BATCH ? kRefillBatch : kRefillLane;
+    H->running = 1;  // the first level runs (the scheduler sets it from then on)
     H->pair_cap = r.cap;
     for (int p = 0; p < 3; ++p) H->ph_t0[p] = ~0ull;
     const uint64_t waves = r.S / (64ull * r.WB) + 2;
@@ -2318,30 +2348,53 @@ int run_enqueue(Run& r) {
     } else if (r.o.launch == FBPT_LAUNCH_PERSISTENT) {
         rc = run_persistent(r.E, st);
     } else {
-        // host-driven levels: the expand launches are bracketed by CUDA events
-        // (the level waits for the host anyway), summed into ms_expand_events
-        cudaEvent_t ex0 = nullptr, ex1 = nullptr;
-        if (cudaEventCreate(&ex0) != cudaSuccess || cudaEventCreate(&ex1) != cudaSuccess) {
-            if (ex0) cudaEventDestroy(ex0);
+        // host-driven levels, one level queued ahead of the one the host waits
+        // for: level L + 1 is enqueued before the host reads level L's loop
+        // condition, and its kernels return at once (gated) if level L ended
+        // the run.  So the stream is busy when a level is enqueued, and the
+        // CUDA events around each level's expand launches bracket the kernels
+        // rather than the host's launch latency; their times are summed into
+        // ms_expand_events for the levels that ran.
+        Eng eg = r.E;
+        eg.gated = 1;
+        cudaEvent_t ex[4] = {}, done[2] = {};
+        bool ev_ok = true;
+        for (auto& e : ex) ev_ok = ev_ok && cudaEventCreate(&e) == cudaSuccess;
+        for (auto& e : done) ev_ok = ev_ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+        auto destroy = [&]() {
+            for (auto& e : ex) if (e) cudaEventDestroy(e);
+            for (auto& e : done) if (e) cudaEventDestroy(e);
+        };
+        if (!ev_ok) {
+            destroy();
             cudaGetLastError();
             return fail(FBPT_ECUDA, "level loop: event create failed");
         }
         r.expand_event_ms = 0.0;
-        for (;;) {
-            rc = launch_level(r.E, st, r.blocks, ex0, ex1);
+        auto enqueue = [&](uint64_t L) -> int {
+            const int b = (int)(L & 1);
+            FBPT_TRY(launch_level(eg, st, r.blocks, ex[2 * b], ex[2 * b + 1]));
+            FBPT_CUDA_TRY(cudaMemcpyAsync(&r.H->host_flag[b], &ws->ctl->running, sizeof(unsigned),
+                                          cudaMemcpyDeviceToHost, st));
+            FBPT_CUDA_TRY(cudaEventRecord(done[b], st));
+            return FBPT_OK;
+        };
+        rc = enqueue(0);
+        for (uint64_t L = 0; rc == FBPT_OK; ++L) {
+            rc = enqueue(L + 1);
             if (rc != FBPT_OK) break;
-            if (cudaMemcpyAsync(&r.H->running, &ws->ctl->running, sizeof(unsigned), cudaMemcpyDeviceToHost, st) !=
-                    cudaSuccess ||
-                cudaStreamSynchronize(st) != cudaSuccess) {
+            const int b = (int)(L & 1);
+            if (cudaEventSynchronize(done[b]) != cudaSuccess) {
                 rc = fail(FBPT_ECUDA, std::string("level loop: ") + cudaGetErrorString(cudaGetLastError()));
                 break;
             }
             float ms = 0.f;
-            if (cudaEventElapsedTime(&ms, ex0, ex1) == cudaSuccess) r.expand_event_ms += ms;
-            if (!r.H->running) break;
+            if (cudaEventElapsedTime(&ms, ex[2 * b], ex[2 * b + 1]) == cudaSuccess) r.expand_event_ms += ms;
+            if (!r.H->host_flag[b]) break;
         }
-        cudaEventDestroy(ex0);
-        cudaEventDestroy(ex1);
+        if (cudaStreamSynchronize(st) != cudaSuccess && rc == FBPT_OK)
+            rc = fail(FBPT_ECUDA, std::string("level loop: ") + cudaGetErrorString(cudaGetLastError()));
+        destroy();
         if (rc == FBPT_OK) rc = launch_final_sweep(r.E, st, r.blocks);
     }
     if (rc != FBPT_OK) return rc;
@@ -2773,6 +2826,9 @@ int autotune_impl(fbpt_graph* g, uint64_t seed, uint64_t S, const fbpt_opts* bas
             best_wb = WB;
         }
     }
+    // a smaller grid is kept only if it is more than 3% faster than the best so
+    // far: the probe runs few samples, whose small frontiers favour small grids
+    // more than a full-size run's do
     const int full = launch_shape().level_blocks;
     uint32_t best_blocks = (uint32_t)full;
     double best_rate = best;
@@ -2780,7 +2836,7 @@ int autotune_impl(fbpt_graph* g, uint64_t seed, uint64_t S, const fbpt_opts* bas
         const uint32_t blocks = (uint32_t)std::max(1, full / div);
         double rate = 0;
         FBPT_TRY(probe(best_wb, blocks, rate, o.schedule));
-        if (rate >= 0.97 * best) {
+        if (rate > 1.03 * best_rate) {
             best_blocks = blocks;
             best_rate = rate;
         }

@@ -75,6 +75,7 @@ struct Ctl {
     unsigned int pend_count;         // vertices whose next row changed this level
     unsigned int chunk_next;         // expand's dynamic chunk counter
     unsigned int running;            // loop condition
+    unsigned int host_flag[2];       // host mirror only: the loop condition after even / odd levels
     unsigned int error;              // ErrorBits
     unsigned int refill;             // RefillMode
     unsigned int bar_count, bar_gen; // grid barrier of the persistent kernel
@@ -204,6 +205,8 @@ struct Eng {
     fbpt_trace_row* trace;        // device copy of the per-level trace (NULL = off)
     uint64_t trace_cap;
     unsigned long long cond;      // cudaGraphConditionalHandle (0 = host-driven loop)
+    uint32_t gated;               // host loop: the level kernels return at once when the run has ended
+    uint32_t gated_pad;
     unsigned long long spin_limit;  // bounded waits of the persistent kernel's grid barrier
     // vertex order: rows of vertex label w are [rstart[w], rend[w]) (row_ptr and
     // row_ptr + 1 for the identity); perm maps a start vertex to its label and
