@@ -117,13 +117,16 @@ struct Smem {
 
 // dst[0 .. count) = src[0 .. count) (count <= kMaxLanes + 1), all loads of a
 // thread issued before any store so that they are in flight together.
+// ro: src does not change while the kernel runs (read through L1, so that the
+// CTAs of an SM share one fetch).
+template <bool ro = false>
 __device__ __forceinline__ void fill_smem(uint32_t* dst, const uint32_t* src, uint32_t count) {
     constexpr uint32_t kPer = (kMaxLanes + 1 + kThreads - 1) / kThreads;
     uint32_t v[kPer];
 #pragma unroll
     for (uint32_t k = 0; k < kPer; ++k) {
         const uint32_t i = threadIdx.x + k * kThreads;
-        v[k] = i < count ? L2(&src[i]) : 0u;
+        v[k] = i < count ? LD<ro>(&src[i]) : 0u;
     }
 #pragma unroll
     for (uint32_t k = 0; k < kPer; ++k) {
@@ -182,27 +185,28 @@ __device__ __forceinline__ void sweep_entry(const Eng& E, const uint64_t* fin, u
 
 // pre: shared memory for the finished lanes' entry prefixes (kMaxLanes + 1);
 // fin: shared memory for the finished-lane masks (kMaxWords).
+template <bool ro>
 __device__ void dev_sweep(const Eng& E, uint32_t* pre, uint64_t* fin) {
     Ctl* ctl = E.ctl;
-    const uint32_t F = L2(&ctl->fin_count);
-    const uint32_t spill = L2(&ctl->spill_sweep);
+    const uint32_t F = LD<ro>(&ctl->fin_count);
+    const uint32_t spill = LD<ro>(&ctl->spill_sweep);
     if (F == 0 && !spill) return;
     {
         // a CTA whose first index lies beyond both entry ranges has nothing to do
-        uint64_t work = L2(&ctl->fin_pre[F]);
-        if (spill) work = max(work, min((uint64_t)L2(&ctl->spill_len[L2(&ctl->spill_cur) ^ 1u]), E.spill_cap));
+        uint64_t work = LD<ro>(&ctl->fin_pre[F]);
+        if (spill) work = max(work, min((uint64_t)L2(&ctl->spill_len[LD<ro>(&ctl->spill_cur) ^ 1u]), E.spill_cap));
         if ((uint64_t)blockIdx.x * blockDim.x >= work) return;
     }
     phase_begin(ctl, 2);
     __syncthreads();
-    fill_smem(pre, ctl->fin_pre, F + 1);
-    for (uint32_t i = threadIdx.x; i < E.WB; i += blockDim.x) fin[i] = L2(&ctl->fin_mask[i]);
+    fill_smem<ro>(pre, ctl->fin_pre, F + 1);
+    for (uint32_t i = threadIdx.x; i < E.WB; i += blockDim.x) fin[i] = LD<ro>(&ctl->fin_mask[i]);
     __syncthreads();
     const uint32_t total = pre[F];
     const uint32_t lane = lane_id();
     const uint64_t wid = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarp = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    const uint64_t cap = L2(&ctl->pair_cap);
+    const uint64_t cap = LD<ro>(&ctl->pair_cap);
     for (uint64_t base = wid * 32; base < total; base += nwarp * 32) {
         const uint32_t idx = (uint32_t)(base + lane);
         if (idx < total) {
@@ -211,18 +215,18 @@ __device__ void dev_sweep(const Eng& E, uint32_t* pre, uint64_t* fin) {
                 const uint32_t mid = (lo + hi) >> 1;
                 if (pre[mid] <= idx) lo = mid; else hi = mid;
             }
-            const uint32_t l = L2(&ctl->fin_lane[lo]);
+            const uint32_t l = LD<ro>(&ctl->fin_lane[lo]);
             const uint32_t p = idx - pre[lo];
             const uint32_t v = L2(&E.seg[(uint64_t)l * E.seg_cap + p]);
-            const uint64_t dst = L2(&ctl->lane_base[l]) + p;
+            const uint64_t dst = LD<ro>(&ctl->lane_base[l]) + p;
             const uint32_t vo = E.inv ? __ldg(&E.inv[v]) : v;
             if (dst < cap) E.rows_v[dst] = vo;
             sweep_entry(E, fin, l, v, vo);
         }
     }
     if (spill) {
-        const uint32_t dst = L2(&ctl->spill_cur), src = dst ^ 1u;
-        const uint64_t len = min((uint64_t)L2(&ctl->spill_len[src]), E.spill_cap);
+        const uint32_t dst = LD<ro>(&ctl->spill_cur), src = dst ^ 1u;
+        const uint64_t len = min((uint64_t)LD<ro>(&ctl->spill_len[src]), E.spill_cap);
         for (uint64_t base = wid * 32; base < len; base += nwarp * 32) {
             const uint64_t idx = base + lane;
             const bool ok = idx < len;
@@ -239,7 +243,7 @@ __device__ void dev_sweep(const Eng& E, uint32_t* pre, uint64_t* fin) {
             }
             const uint64_t kp = warp_alloc<unsigned long long>(&ctl->spill_len[dst], (ok && !done) ? 1ull : 0ull);
             if (ok && done) {
-                const uint64_t d = L2(&ctl->lane_base[l]) + p;
+                const uint64_t d = LD<ro>(&ctl->lane_base[l]) + p;
                 const uint32_t vo = E.inv ? __ldg(&E.inv[v]) : v;
                 if (d < cap) E.rows_v[d] = vo;
                 sweep_entry(E, fin, l, v, vo);
@@ -528,13 +532,18 @@ __device__ __forceinline__ void expand_wide(const Eng& E, const uint32_t* lane_j
         uint4 ra = make_uint4(0u, 0u, 0u, 0u), rb = ra;
         bool pre = false;  // this chunk's vectors are in the slot
         for (uint32_t c = c0; c < c1; ++c) {
-            const uint32_t uc = LD<ro>(&E.wide_chunk[c]);
+            // the level's chunks are taken from the last allocated down: the
+            // commit warps that allocate last are those with the most items,
+            // i.e. the units reached by the most colours, whose chunks are the
+            // longest; started first, they no longer make the level's tail
+            const uint32_t cr = (uint32_t)(NC - 1) - c;
+            const uint32_t uc = LD<ro>(&E.wide_chunk[cr]);
             if (uc != u) {
                 u = uc;
                 ra = LD<ro>(&E.wide_rec[2ull * u]);
                 rb = LD<ro>(&E.wide_rec[2ull * u + 1]);
             }
-            const WidePos P = wide_pos(c, ra, rb, lane);
+            const WidePos P = wide_pos(cr, ra, rb, lane);
             uint4 ta = make_uint4(0u, 0u, 0u, 0u), tb = ta, ca = ta, cbv = ta;
             if (pre) {
                 cp_async_wait_all();
@@ -560,10 +569,10 @@ __device__ __forceinline__ void expand_wide(const Eng& E, const uint32_t* lane_j
             // the next chunk of the grab, if it continues this unit: its vectors
             // head for the slot while this chunk draws
             pre = false;
-            if (c + 1 < c1 && LD<ro>(&E.wide_chunk[c + 1]) == u) {
+            if (c + 1 < c1 && LD<ro>(&E.wide_chunk[cr - 1]) == u) {
                 sl ^= 1u;
                 uint4* slot = stage + (sl * 32 + lane) * 4;
-                const WidePos Pn = wide_pos(c + 1, ra, rb, lane);
+                const WidePos Pn = wide_pos(cr - 1, ra, rb, lane);
                 if (Pn.vma) {
                     cp_async16(&slot[0], thr4 + Pn.q);
                     cp_async16(&slot[1], col4 + Pn.q);
@@ -851,20 +860,24 @@ enum ExpandPart : int { kPartPush = 0, kPartAlt = 1, kPartAll = 2 };
 template <int part>
 __device__ void dev_expand(const Eng& E, uint32_t* lane_j, uint32_t* pcnt, uint32_t* pbuf, uint4* pstage) {
     Ctl* ctl = E.ctl;
-    const uint64_t G = L2(&ctl->list_groups);
-    const uint64_t NW = L2(&ctl->wide_chunks);
-    const uint32_t dir = L2(&ctl->dir);
+    // the level's control fields do not change during a per-level kernel:
+    // read through L1 there, so that an SM's warps share one fetch
+    constexpr bool ro = part != kPartAll;
+    const uint64_t G = LD<ro>(&ctl->list_groups);
+    const uint64_t NW = LD<ro>(&ctl->wide_chunks);
+    const uint32_t dir = LD<ro>(&ctl->dir);
     const bool pull = dir == kDirPull && E.frontd;
     if (part == kPartPush && dir != kDirPush) return;
     if (part == kPartAlt && (dir == kDirPush || E.model == FBPT_MODEL_LT)) return;
     if (G == 0 && NW == 0) return;
-    const uint64_t U = L2(&ctl->list_count);
+    const uint64_t U = LD<ro>(&ctl->list_count);
     const uint64_t nchunks = (G + kChunk - 1) / kChunk;
     // overflow already flagged by commit
-    if (nchunks > E.chunk_cap || U > E.list_cap || NW > E.wide_chunk_cap || L2(&ctl->wide_units) > E.list_cap) return;
+    if (nchunks > E.chunk_cap || U > E.list_cap || NW > E.wide_chunk_cap || LD<ro>(&ctl->wide_units) > E.list_cap)
+        return;
     phase_begin(ctl, 0);
     __syncthreads();
-    fill_smem(lane_j, ctl->lane_j, 64u * E.WB);
+    fill_smem<ro>(lane_j, ctl->lane_j, 64u * E.WB);
     const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
     uint32_t* cnt = pcnt + warp;
     uint32_t* buf = pbuf + warp * kPendBuf;
@@ -884,7 +897,7 @@ __device__ void dev_expand(const Eng& E, uint32_t* lane_j, uint32_t* pcnt, uint3
     }
 #endif
     uint64_t n_edges = 0, n_calls = 0;
-    const bool scan = L2(&ctl->mode) == FBPT_COMPACT_SCAN;
+    const bool scan = LD<ro>(&ctl->mode) == FBPT_COMPACT_SCAN;
     if (E.model == FBPT_MODEL_LT) {
         expand_lt<part != kPartAll>(E, lane_j, K, U, n_edges, n_calls);
     } else if (part != kPartPush && pull) {
@@ -938,10 +951,13 @@ __device__ __forceinline__ uint32_t nth_bit64(uint64_t m, uint32_t r) {
 // warp's 32 vertices are spread over its lanes, so a hub reached by many
 // colours at once is not left to one thread.  Non-empty rows become frontier
 // units (if w has in-edges).
+// ro: the per-level kernel, in which the level's control fields do not change
+// (read through L1); the persistent kernel reads them through L2.
+template <bool ro>
 __device__ void dev_commit(const Eng& E, Smem& sm) {
     Ctl* ctl = E.ctl;
-    const bool scan = L2(&ctl->mode) == FBPT_COMPACT_SCAN;
-    const uint32_t P = scan ? 0u : (uint32_t)min((uint64_t)L2(&ctl->pend_count), E.pend_cap);
+    const bool scan = LD<ro>(&ctl->mode) == FBPT_COMPACT_SCAN;
+    const uint32_t P = scan ? 0u : (uint32_t)min((uint64_t)LD<ro>(&ctl->pend_count), E.pend_cap);
     // queue: vertices per warp: spread a small level over more warps of the
     // grid (the work is a chain of dependent loads per vertex), but at least
     // FBPT_COMMIT_VPW_MIN per warp so that each warp's fixed bookkeeping stays
@@ -959,7 +975,7 @@ __device__ void dev_commit(const Eng& E, Smem& sm) {
     for (uint32_t i = threadIdx.x; i < 2 * E.WB; i += blockDim.x) sm.act[i] = 0;
     __syncthreads();
     if (P || scan) phase_begin(ctl, 1);
-    const uint32_t spill_cur = L2(&ctl->spill_cur);
+    const uint32_t spill_cur = LD<ro>(&ctl->spill_cur);
     const uint32_t lane = lane_id();
     const uint64_t wid = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     CommitWarp& cw = sm.cw[threadIdx.x >> 5];
@@ -1062,7 +1078,7 @@ __device__ void dev_commit(const Eng& E, Smem& sm) {
         if (E.frontd && units) {  // frontier row by vertex, for a pull level
             for (uint32_t i = 0; i < E.WB; ++i)
                 E.frontd[(uint64_t)w * E.WB + i] = ((occ >> i) & 1ull) ? L2(&E.stage[idx * E.WB + i]) : 0ull;
-            E.fstamp[w] = (uint32_t)L2(&ctl->tick) + 1u;
+            E.fstamp[w] = (uint32_t)LD<ro>(&ctl->tick) + 1u;
         }
         mwords += units ? (E.unfused ? units : (uint64_t)__popcll(occ)) : 0;
         ncol += units ? bits : 0;
@@ -1636,7 +1652,7 @@ __device__ void dev_schedule(const Eng& E, Smem& sm) {
 __global__ void __launch_bounds__(kThreads) k_sweep(const Eng E) {
     __shared__ uint32_t pre[kMaxLanes + 1];
     __shared__ uint64_t fin[kMaxWords];
-    dev_sweep(E, pre, fin);
+    dev_sweep<true>(E, pre, fin);
 }
 // The level's first kernel: the start vertices of the lanes the last schedule
 // refilled, this CTA's share of the sweep of the lanes that finished at the
@@ -1650,7 +1666,7 @@ __global__ void __launch_bounds__(kThreads, FBPT_EXPAND_MINB) k_expand(const Eng
     extern __shared__ uint4 pstage[];  // kStageBytes, dynamic
     if (E.gated && !L2(&E.ctl->running)) return;
     dev_init(E);
-    dev_sweep(E, lane_j, fin);
+    dev_sweep<true>(E, lane_j, fin);
     __syncthreads();
     dev_expand<kPartPush>(E, lane_j, pcnt, pbuf, pstage);
 }
@@ -1664,7 +1680,7 @@ __global__ void __launch_bounds__(kThreads) k_expand_alt(const Eng E) {
 __global__ void __launch_bounds__(kThreads) k_commit(const Eng E) {
     __shared__ Smem sm;
     if (E.gated && !L2(&E.ctl->running)) return;
-    dev_commit(E, sm);
+    dev_commit<true>(E, sm);
 }
 __global__ void __launch_bounds__(kSchedThreads) k_schedule(const Eng E) {
     __shared__ Smem sm;
@@ -1724,15 +1740,15 @@ __global__ void __launch_bounds__(kThreads) k_run(const Eng E) {
     Ctl* ctl = E.ctl;
     unsigned gen = 0;
     for (;;) {
-        dev_sweep(E, sm.lane, sm.fin);  // lanes finished at the previous level
+        dev_sweep<false>(E, sm.lane, sm.fin);  // lanes finished at the previous level
         dev_init(E);       // lanes given a sample at the previous level
         dev_expand<kPartAll>(E, sm.lane, sm.pcnt, sm.pbuf, pstage);
         if (!grid_barrier(E, sm, gen, false)) return;
-        dev_commit(E, sm);
+        dev_commit<false>(E, sm);
         if (!grid_barrier(E, sm, gen, true)) return;
         if (!L2(&ctl->running)) break;
     }
-    dev_sweep(E, sm.lane, sm.fin);
+    dev_sweep<false>(E, sm.lane, sm.fin);
 }
 
 // ---- final CSR: each staged row sorted into its place -----------------------------------
