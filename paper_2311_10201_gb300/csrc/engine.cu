@@ -95,7 +95,7 @@ struct SchedHead {
     unsigned long long next_j, pair_cursor, new_packed, new_colours, tick, tick_limit;
     unsigned long long list_count, list_groups, list_colours;
     unsigned long long wide_packed, wide_gnew, wide_units, wide_groups;
-    unsigned long long ph_t0[3], ph_t1[3];
+    unsigned long long ph_t0[3], ph_t1[3], spill_len[2];
     uint32_t err, refill, sched, dir, frontier_lanes, pend_count, spill_cur, mode, scan_rows;
 };
 
@@ -190,13 +190,10 @@ __device__ void dev_sweep(const Eng& E, uint32_t* pre, uint64_t* fin) {
     Ctl* ctl = E.ctl;
     const uint32_t F = LD<ro>(&ctl->fin_count);
     const uint32_t spill = LD<ro>(&ctl->spill_sweep);
+    // a CTA whose first index lies beyond both entry ranges has nothing to do
+    const uint64_t work = LD<ro>(&ctl->sweep_work);
     if (F == 0 && !spill) return;
-    {
-        // a CTA whose first index lies beyond both entry ranges has nothing to do
-        uint64_t work = LD<ro>(&ctl->fin_pre[F]);
-        if (spill) work = max(work, min((uint64_t)L2(&ctl->spill_len[LD<ro>(&ctl->spill_cur) ^ 1u]), E.spill_cap));
-        if ((uint64_t)blockIdx.x * blockDim.x >= work) return;
-    }
+    if ((uint64_t)blockIdx.x * blockDim.x >= work) return;
     phase_begin(ctl, 2);
     __syncthreads();
     fill_smem<ro>(pre, ctl->fin_pre, F + 1);
@@ -1407,6 +1404,7 @@ __device__ void dev_schedule(const Eng& E, Smem& sm) {
         case 25: h.wide_groups = L2(&ctl->wide_groups); break;
         case 26: h.mode = L2(&ctl->mode); break;
         case 27: h.scan_rows = L2(&ctl->scan_rows); break;
+        case 28: case 29: h.spill_len[t - 28] = L2(&ctl->spill_len[t - 28]); break;
         default: break;
     }
     uint32_t per = 1;
@@ -1580,6 +1578,9 @@ __device__ void dev_schedule(const Eng& E, Smem& sm) {
             ctl->spill_len[dst] = 0;
         }
         ctl->spill_sweep = any_spill ? 1u : 0u;
+        // the sweep reads the log the commit just appended to (the buffer that
+        // was current before the flip)
+        ctl->sweep_work = max(S64, any_spill ? min(h.spill_len[h.spill_cur], (unsigned long long)E.spill_cap) : 0ull);
         const unsigned long long tick = h.tick;
         if (E.trace && tick < E.trace_cap) {
             fbpt_trace_row& row = E.trace[tick];

@@ -101,6 +101,7 @@ struct Ctl {
     unsigned long long fin_mask[kMaxWords]; // finished lanes as a bitmap (spill-log sweep)
     unsigned int spill_cur, spill_sweep;   // spill log buffer commit appends to; sweep it this level
     unsigned long long spill_len[2];
+    unsigned long long sweep_work;   // entries the coming sweep reads (segments or spill log, the larger)
     // counters
     unsigned long long st_edges, st_calls, st_units, st_cev, st_assigned, st_push, st_pull, st_mask_words;
     unsigned long long st_groups;
