@@ -1417,11 +1417,25 @@ __device__ void dev_schedule(const Eng& E, Smem& sm) {
         act = L2(&ctl->act_w[wi]);
     }
     uint32_t cnt[kPer], jj[kPer];
+    if (kPer % 4 == 0 && (per & 3u) == 0) {
+        // runs of four lanes: one 16-byte load per array and four lanes
 #pragma unroll
-    for (uint32_t c = 0; c < kPer; ++c) {
-        const bool in = a0 + c < a1;
-        cnt[c] = in ? L2(&ctl->lane_cnt[a0 + c]) : 0u;
-        jj[c] = in ? L2(&ctl->lane_j[a0 + c]) : 0u;
+        for (uint32_t q = 0; q < kPer / 4; ++q) {
+            uint4 c4 = make_uint4(0u, 0u, 0u, 0u), j4 = c4;
+            if (4 * q < per && a0 < a1) {
+                c4 = __ldcg(reinterpret_cast<const uint4*>(&ctl->lane_cnt[a0 + 4 * q]));
+                j4 = __ldcg(reinterpret_cast<const uint4*>(&ctl->lane_j[a0 + 4 * q]));
+            }
+            cnt[4 * q] = c4.x; cnt[4 * q + 1] = c4.y; cnt[4 * q + 2] = c4.z; cnt[4 * q + 3] = c4.w;
+            jj[4 * q] = j4.x; jj[4 * q + 1] = j4.y; jj[4 * q + 2] = j4.z; jj[4 * q + 3] = j4.w;
+        }
+    } else {
+#pragma unroll
+        for (uint32_t c = 0; c < kPer; ++c) {
+            const bool in = a0 + c < a1;
+            cnt[c] = in ? L2(&ctl->lane_cnt[a0 + c]) : 0u;
+            jj[c] = in ? L2(&ctl->lane_j[a0 + c]) : 0u;
+        }
     }
     // the schedule network's parameters (learned schedule only) into shared
     // memory, loaded together with the fields above (blockDim >= kThreads)

@@ -89,8 +89,8 @@ struct Ctl {
     unsigned long long act_w[kMaxWords];   // lanes present in the new frontier
     unsigned long long init_w[kMaxWords];  // lanes given a sample at the last schedule (init input)
     unsigned long long still_w[kMaxWords]; // lanes with colours in the current frontier
-    unsigned int lane_j[kMaxLanes];        // sample index held by each lane
-    unsigned int lane_cnt[kMaxLanes];      // RR entries of the lane's current sample so far
+    alignas(16) unsigned int lane_j[kMaxLanes];        // sample index held by each lane
+    alignas(16) unsigned int lane_cnt[kMaxLanes];      // RR entries of the lane's current sample so far
     unsigned int retired_j[kMaxLanes];     // sample index a finished lane held
     unsigned long long lane_base[kMaxLanes]; // staging position of a finished lane's row
     // sweep input, written by the schedule: finished lanes and the prefix of
