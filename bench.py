@@ -31,11 +31,11 @@ import synth  # noqa: E402
 WORKLOAD = "rmat_s22_wc"
 # DRAM bytes (read + write) per 4-edge group of a k_expand launch (start
 # vertices, expand and sweep), from an ncu capture of the current kernel on the
-# s22 workload in degree order (five launches, levels 600-604: 764,330,752 B over
+# s22 workload in degree order (five launches, levels 600-604: 774,605,568 B over
 # 21,148,211 groups); the bench scales it by its own groups per launch.  None
 # when the kernel has changed since the capture.
-EXPAND_DRAM_BYTES_PER_GROUP = ((151961344 + 151427328 + 152355328 + 151352320 + 151691776) +
-                               (3368704 + 489984 + 512256 + 743936 + 427776)) / 21148211
+EXPAND_DRAM_BYTES_PER_GROUP = ((151928064 + 151410432 + 152340480 + 151315456 + 151691776) +
+                               (5537024 + 2370560 + 2382848 + 2449920 + 3179008)) / 21148211
 EXPAND_TRAFFIC_NOTE = ("ncu dram__bytes_read + dram__bytes_write per group of the current kernel "
                        "(s22, degree order, levels 600-604) x this run's groups per launch")
 METRIC = "RR samples/s (bit-exact RR sets + greedy seeds, R-MAT s22 WC, 1,048,576 samples, k=100)"
@@ -615,7 +615,7 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = cpu_baseline(g, seed, 8192)
+        cpu = cpu_baseline(g, seed, 40960)  # about 10 s of the oracle on 16 cores
 
     # kernels per step: 3 or 4 per level (expand with start vertices and sweep,
     # commit, scheduler; + the filtered/pull expand when the schedule may pick
