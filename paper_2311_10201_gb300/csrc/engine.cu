@@ -906,11 +906,24 @@ __device__ void dev_expand(const Eng& E, uint32_t* lane_j, uint32_t* pcnt, uint3
         expand_wide<false, part != kPartAll>(E, lane_j, K, NW, scan, cnt, buf, wstage, n_edges, n_calls);
         expand_push<false, part != kPartAll>(E, lane_j, K, G, U, nchunks, scan, cnt, buf, n_edges, n_calls);
     }
+    // one reduction per CTA for the statistics (the lane table's shared
+    // memory holds the warps' sums once every warp is done with it)
     n_edges = warp_sum(n_edges);
     n_calls = warp_sum(n_calls);
+    __syncthreads();
     if (lane == 0) {
-        if (n_edges) atomicAdd(&ctl->st_edges, (unsigned long long)n_edges);
-        if (n_calls) atomicAdd(&ctl->st_calls, (unsigned long long)n_calls);
+        lane_j[2 * warp] = (uint32_t)n_edges;
+        lane_j[2 * warp + 1] = (uint32_t)n_calls;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long e = 0, c = 0;
+        for (uint32_t k = 0; k < (blockDim.x >> 5); ++k) {
+            e += lane_j[2 * k];
+            c += lane_j[2 * k + 1];
+        }
+        if (e) atomicAdd(&ctl->st_edges, e);
+        if (c) atomicAdd(&ctl->st_calls, c);
     }
     phase_end(ctl, 0);
 }
@@ -1238,12 +1251,27 @@ __device__ void dev_commit(const Eng& E, Smem& sm) {
             m = mnext;
         }
     }
+    // one reduction per CTA for the statistics and colour / group totals
     mwords = warp_sum(mwords);
     ncol = warp_sum(ncol);
     wgroups = warp_sum(wgroups);
-    if (lane == 0 && mwords) atomicAdd(&ctl->st_mask_words, (unsigned long long)mwords);
-    if (lane == 0 && ncol) atomicAdd(&ctl->new_colours, (unsigned long long)ncol);
-    if (lane == 0 && wgroups) atomicAdd(&ctl->wide_gnew, (unsigned long long)wgroups);
+    if (lane == 0) {
+        sm.mscan[threadIdx.x >> 5][0] = mwords;
+        sm.mscan[threadIdx.x >> 5][1] = ncol;
+        sm.mscan[threadIdx.x >> 5][2] = wgroups;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long a = 0, b = 0, c = 0;
+        for (uint32_t k = 0; k < (blockDim.x >> 5); ++k) {
+            a += sm.mscan[k][0];
+            b += sm.mscan[k][1];
+            c += sm.mscan[k][2];
+        }
+        if (a) atomicAdd(&ctl->st_mask_words, a);
+        if (b) atomicAdd(&ctl->new_colours, b);
+        if (c) atomicAdd(&ctl->wide_gnew, c);
+    }
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < E.WB; i += blockDim.x) {
         const unsigned long long a = ((unsigned long long)sm.act[2 * i + 1] << 32) | sm.act[2 * i];

@@ -69,11 +69,16 @@ enum RefillMode : uint32_t {
 // Device-resident control block of one sampling run.  Written and read only
 // by the engine's kernels (and by the host between runs).
 struct Ctl {
-    unsigned long long list_count;   // frontier units for the coming expand
+    // The counters that kernels take returned atomics on (the expand's chunk
+    // counters and pending count, the commit's allocation counters) each start
+    // a 128-byte line of their own, apart from the statistics and the fields
+    // that all CTAs reduce into: a returned atomic or a load queues behind the
+    // reductions on its line.
+    alignas(128) unsigned int pend_count;  // vertices whose next row changed this level
+    alignas(128) unsigned int chunk_next;  // expand's dynamic chunk counter
+    alignas(128) unsigned long long new_packed;  // commit's allocation counter (units | groups << 26)
+    alignas(128) unsigned long long list_count;  // frontier units for the coming expand
     unsigned long long list_groups;  // their total 4-edge groups
-    unsigned long long new_packed;   // commit's allocation counter (units | groups << 26)
-    unsigned int pend_count;         // vertices whose next row changed this level
-    unsigned int chunk_next;         // expand's dynamic chunk counter
     unsigned int running;            // loop condition
     unsigned int host_flag[2];       // host mirror only: the loop condition after even / odd levels
     unsigned int error;              // ErrorBits
@@ -103,21 +108,25 @@ struct Ctl {
     unsigned long long spill_len[2];
     unsigned long long sweep_work;   // entries the coming sweep reads (segments or spill log, the larger)
     // counters
-    unsigned long long st_edges, st_calls, st_units, st_cev, st_assigned, st_push, st_pull, st_mask_words;
+    alignas(128) unsigned long long st_edges;
+    unsigned long long st_calls, st_units, st_cev, st_assigned, st_push, st_pull, st_mask_words;
     unsigned long long st_groups;
     unsigned long long new_colours, list_colours;  // colour bits of the new / current frontier units
     // wide units: the commit's allocation counter (units | chunks << 26) and
     // their groups; the coming expand's units, chunks and groups; its chunk counter
-    unsigned long long wide_packed, wide_gnew;
+    alignas(128) unsigned long long wide_packed;
+    alignas(128) unsigned long long wide_gnew;
     unsigned long long wide_units, wide_chunks, wide_groups;
-    unsigned int wchunk_next, wpad;
+    alignas(128) unsigned int wchunk_next;
+    unsigned int wpad;
     unsigned long long wide_need;  // largest wide-chunk count a level asked for beyond the capacity
     // compaction of the coming level (fbpt_compaction); stage rows the scan
     // commit has handed out
-    unsigned int mode, scan_rows;
+    unsigned int mode;
+    alignas(128) unsigned int scan_rows;
     // phase times: first CTA start .. last CTA end of each phase (%globaltimer, ns);
     // index 0 expand, 1 commit, 2 sweep
-    unsigned long long ph_t0[3], ph_t1[3], st_phase_ns[3];
+    alignas(128) unsigned long long ph_t0[3], ph_t1[3], st_phase_ns[3];
 };
 
 // Per-graph, per-shape working memory.  Every array is all-zero between runs
