@@ -31,11 +31,11 @@ import synth  # noqa: E402
 WORKLOAD = "rmat_s22_wc"
 # DRAM bytes (read + write) per 4-edge group of a k_expand launch (start
 # vertices, expand and sweep), from an ncu capture of the current kernel on the
-# s22 workload in degree order (five launches, levels 600-604: 774,605,568 B over
+# s22 workload in degree order (five launches, levels 600-604: 774,158,592 B over
 # 21,148,211 groups); the bench scales it by its own groups per launch.  None
 # when the kernel has changed since the capture.
-EXPAND_DRAM_BYTES_PER_GROUP = ((151928064 + 151410432 + 152340480 + 151315456 + 151691776) +
-                               (5537024 + 2370560 + 2382848 + 2449920 + 3179008)) / 21148211
+EXPAND_DRAM_BYTES_PER_GROUP = ((151935488 + 151389696 + 152336640 + 151331328 + 151704320) +
+                               (5079808 + 2358016 + 2384128 + 2474752 + 3164416)) / 21148211
 EXPAND_TRAFFIC_NOTE = ("ncu dram__bytes_read + dram__bytes_write per group of the current kernel "
                        "(s22, degree order, levels 600-604) x this run's groups per launch")
 METRIC = "RR samples/s (bit-exact RR sets + greedy seeds, R-MAT s22 WC, 1,048,576 samples, k=100)"
