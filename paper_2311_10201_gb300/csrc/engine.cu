@@ -1411,33 +1411,53 @@ __device__ void dev_schedule(const Eng& E, Smem& sm) {
     // the lane masks of each word and the counts and sample ids of this
     // thread's lanes.  per: the smallest power of two with per * blockDim >= L
     // (per <= kPer by the launch shape), so that a run never straddles two words.
-    switch (t) {
-        case 0: h.err = L2(&ctl->error); break;
-        case 1: h.next_j = L2(&ctl->next_j); break;
-        case 2: h.pair_cursor = L2(&ctl->pair_cursor); break;
-        case 3: h.refill = L2(&ctl->refill); break;
-        case 4: h.new_packed = L2(&ctl->new_packed); break;
-        case 5: h.new_colours = L2(&ctl->new_colours); break;
-        case 6: h.sched = L2(&ctl->sched); break;
-        case 7: h.tick = L2(&ctl->tick); break;
-        case 8: h.list_groups = L2(&ctl->list_groups); break;
-        case 9: h.list_count = L2(&ctl->list_count); break;
-        case 10: h.list_colours = L2(&ctl->list_colours); break;
-        case 11: h.pend_count = L2(&ctl->pend_count); break;
-        case 12: h.dir = L2(&ctl->dir); break;
-        case 13: h.frontier_lanes = L2(&ctl->frontier_lanes); break;
-        case 14: h.spill_cur = L2(&ctl->spill_cur); break;
-        case 15: h.tick_limit = L2(&ctl->tick_limit); break;
-        case 16: case 17: case 18: h.ph_t0[t - 16] = L2(&ctl->ph_t0[t - 16]); break;
-        case 19: case 20: case 21: h.ph_t1[t - 19] = L2(&ctl->ph_t1[t - 19]); break;
-        case 22: h.wide_packed = L2(&ctl->wide_packed); break;
-        case 23: h.wide_gnew = L2(&ctl->wide_gnew); break;
-        case 24: h.wide_units = L2(&ctl->wide_units); break;
-        case 25: h.wide_groups = L2(&ctl->wide_groups); break;
-        case 26: h.mode = L2(&ctl->mode); break;
-        case 27: h.scan_rows = L2(&ctl->scan_rows); break;
-        case 28: case 29: h.spill_len[t - 28] = L2(&ctl->spill_len[t - 28]); break;
-        default: break;
+    // (one lane in each of four warps, its loads issued back to back before
+    // any is stored: a switch over the lanes of one warp ran its cases one
+    // after another, each waiting for its load, ~6 us per level)
+    if ((t & 31u) == 0u && (t >> 5) < 4u) {
+        switch (t >> 5) {
+            case 0: {
+                const uint32_t err = L2(&ctl->error), refill = L2(&ctl->refill), sched = L2(&ctl->sched);
+                const unsigned long long nj = L2(&ctl->next_j), pc = L2(&ctl->pair_cursor);
+                const unsigned long long np = L2(&ctl->new_packed), nc = L2(&ctl->new_colours), tk = L2(&ctl->tick);
+                h.err = err; h.refill = refill; h.sched = sched;
+                h.next_j = nj; h.pair_cursor = pc; h.new_packed = np; h.new_colours = nc; h.tick = tk;
+                break;
+            }
+            case 1: {
+                const unsigned long long lg = L2(&ctl->list_groups), lc = L2(&ctl->list_count);
+                const unsigned long long lcol = L2(&ctl->list_colours), tl = L2(&ctl->tick_limit);
+                const uint32_t pend = L2(&ctl->pend_count), dir = L2(&ctl->dir), fl = L2(&ctl->frontier_lanes);
+                const uint32_t sc = L2(&ctl->spill_cur);
+                h.list_groups = lg; h.list_count = lc; h.list_colours = lcol; h.tick_limit = tl;
+                h.pend_count = pend; h.dir = dir; h.frontier_lanes = fl; h.spill_cur = sc;
+                break;
+            }
+            case 2: {
+                unsigned long long a[3], b[3];
+#pragma unroll
+                for (int p = 0; p < 3; ++p) {
+                    a[p] = L2(&ctl->ph_t0[p]);
+                    b[p] = L2(&ctl->ph_t1[p]);
+                }
+                const uint32_t md = L2(&ctl->mode), sr = L2(&ctl->scan_rows);
+#pragma unroll
+                for (int p = 0; p < 3; ++p) {
+                    h.ph_t0[p] = a[p];
+                    h.ph_t1[p] = b[p];
+                }
+                h.mode = md; h.scan_rows = sr;
+                break;
+            }
+            default: {
+                const unsigned long long wp = L2(&ctl->wide_packed), wg = L2(&ctl->wide_gnew);
+                const unsigned long long wu = L2(&ctl->wide_units), wgr = L2(&ctl->wide_groups);
+                const unsigned long long s0 = L2(&ctl->spill_len[0]), s1 = L2(&ctl->spill_len[1]);
+                h.wide_packed = wp; h.wide_gnew = wg; h.wide_units = wu; h.wide_groups = wgr;
+                h.spill_len[0] = s0; h.spill_len[1] = s1;
+                break;
+            }
+        }
     }
     uint32_t per = 1;
     while (per * blockDim.x < L) per <<= 1;
