@@ -1563,17 +1563,24 @@ __device__ void dev_schedule(const Eng& E, Smem& sm) {
     const unsigned long long N64 = may_refill ? tot[3] : 0ull;
     const unsigned long long assigned = N64 < avail ? N64 : avail;
     if (may_refill) {
+        // the sample indices of this thread's refills are loaded together, then
+        // stored (a store per load in one loop waited for each load in turn)
         unsigned long long r = sv[3], got = 0;
+        uint32_t jv[kPer];
 #pragma unroll
         for (uint32_t c = 0; c < kPer; ++c) {
+            jv[c] = 0;
             if ((freem >> c) & 1ull) {
                 if (r < avail) {
-                    ctl->lane_j[a0 + c] = E.order ? __ldg(&E.order[h.next_j + r]) : (uint32_t)(h.next_j + r);
+                    jv[c] = E.order ? __ldg(&E.order[h.next_j + r]) : (uint32_t)(h.next_j + r);
                     got |= 1ull << c;
                 }
                 ++r;
             }
         }
+#pragma unroll
+        for (uint32_t c = 0; c < kPer; ++c)
+            if ((got >> c) & 1ull) ctl->lane_j[a0 + c] = jv[c];
         if (got) atomicOr(&sm.init[wi], got << (a0 & 63));
     }
     __syncthreads();
