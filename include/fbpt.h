@@ -201,9 +201,11 @@ typedef struct fbpt_stats {
                                      to last CTA end (%globaltimer), summed */
     double ms_commit;             /* same for the commit phase */
     double ms_sweep;              /* same for the sweep phase (RR pairs of finished lanes) */
-    double ms_expand_events;      /* FBPT_LAUNCH_HOST only: the expand launches' time measured by CUDA
-                                     events recorded around them on the run's stream, summed (0 for
-                                     the other launch forms, whose levels run inside one launch) */
+    double ms_expand_events;      /* FBPT_LAUNCH_HOST only: the time of each level's expand kernel
+                                     (start vertices, sweep, expand) measured by CUDA events recorded
+                                     around it on the run's stream, summed; the host keeps one level
+                                     queued ahead, so the events bracket the kernels (0 for the other
+                                     launch forms, whose levels run inside one launch) */
 } fbpt_stats;
 
 /* ---- Graphs ---------------------------------------------------------------
@@ -309,7 +311,9 @@ typedef struct fbpt_tuning {
  * a first run of min(S, 4096) samples.  Each shape is warmed up on P / 8
  * samples first.  Row widths 1, 2, 4, ..., 64 words (at most one lane per probe
  * sample), then the best width with 1, 1/2, 1/4 and 1/8 of the resident CTAs:
- * it keeps the fastest width and the fewest CTAs within 3% of its rate.  base supplies the schedule and policy
+ * it keeps the fastest width, and a smaller grid only if it is more than 3%
+ * faster than the best so far (a probe's few samples favour small grids more
+ * than a full run does).  base supplies the schedule and policy
  * (NULL = push); when base->words is set, base->words * base->slots (slots 0
  * read as 1) caps the widths tried.  A learned (or heuristic) schedule is then
  * judged at that shape against the heuristic (or learned, with a policy): the
