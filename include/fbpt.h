@@ -79,7 +79,9 @@ enum fbpt_schedule {
 
 /* How the level loop is driven. */
 enum fbpt_launch {
-    FBPT_LAUNCH_HOST = 0,  /* host launches each level and reads the frontier size back */
+    FBPT_LAUNCH_HOST = 0,  /* host launches each level and reads the loop condition back, one
+                              level queued ahead of the one it waits for (that level's kernels
+                              return at once if the run has ended) */
     FBPT_LAUNCH_GRAPH = 1, /* per-level kernels looped inside one CUDA graph (WHILE conditional node) */
     FBPT_LAUNCH_PERSISTENT = 2 /* one cooperative persistent kernel; levels separated by bounded
                                   grid barriers (FBPT_ETIMEOUT if a wait gives up) */
